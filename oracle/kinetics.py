@@ -1,0 +1,466 @@
+"""CPU oracle: thermochemical source terms and chemical-kinetic Jacobian.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or call anything in ``oracle/``.
+The product path (``paper_1809_01029_gb300``) never imports it and shares no
+code with it; both read the same mechanism *data* produced by ``synth``.
+
+Plain, slow, obviously correct: numpy vectorised over states, Python loops
+over species and reactions, IEEE float64 (or complex128 for complex-step
+differentiation).  Every function names the passage it follows.  The paper's
+equation bodies for the state vector, source terms and Jacobian are not in
+the available text (Sec. 2.2 loads them from a supplement); the forms written
+here are the standard published ones the section names, and the readings are
+listed in the design notes:
+
+* state Phi = [T, S, n_0 .. n_{Ns-2}], S = V (CONP, P fixed) or P (CONV, V
+  fixed); the bath gas Ns-1 is implicit through the ideal-gas law (Sec. 2.2);
+* production rates wdot_k = sum_i nu_ki R_i c_i (Sec. 2.2, production-rate
+  equation);
+* dT/dt from the species enthalpies (CONP) or internal energies (CONV), and
+  dV/dt or dP/dt by differentiating P V = n R T with explicit mass
+  conservation of the bath gas (Sec. 2.2, "volume and pressure source terms");
+* Jacobian J_ij = d f_i / d Phi_j (Sec. 2.2, Jacobian arrangement), computed
+  here by complex-step differentiation of f, i.e. exactly (to rounding) the
+  derivative of the function defined above.
+
+Parity pins (tests/test_oracle_*.py) tie this module to closed forms,
+conservation laws, a computed chemical equilibrium and finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# physical constants (SI with kmol)
+R = 8314.46261815324          # J / (kmol K)
+R_CAL = 1.98720425864083      # cal / (mol K); activation energies are in cal/mol
+P_ATM = 101325.0              # Pa, standard-state pressure of the equilibrium constant
+
+CONP, CONV = 0, 1
+ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI = 0, 1, 2, 3, 4
+
+
+def _re(x):
+    return x.real if np.iscomplexobj(x) else x
+
+
+# ---------------------------------------------------------------------------
+# state -> concentrations (Sec. 2.2: [C]_k = n_k / V, ideal gas P V = n R T)
+# ---------------------------------------------------------------------------
+def concentrations(mech, mode, phi, param):
+    """Return T, V, P, C[Ns, n], Ctot.
+
+    The bath gas concentration is C_tot - sum_{k<Ns-1} C_k with the sum taken
+    sequentially in species order (the implicit last species of Sec. 2.2).
+    """
+    ns = mech.n_species
+    T = phi[0]
+    if mode == CONP:
+        V, P = phi[1], param
+    else:
+        P, V = phi[1], param
+    C = np.empty((ns,) + np.shape(T), dtype=np.result_type(phi, param))
+    for k in range(ns - 1):
+        C[k] = phi[2 + k] / V
+    Ctot = P / (R * T)
+    acc = np.zeros_like(C[0])
+    for k in range(ns - 1):
+        acc = acc + C[k]
+    C[ns - 1] = Ctot - acc
+    return T, V, P, C, Ctot
+
+
+# ---------------------------------------------------------------------------
+# thermodynamics: NASA 7-coefficient polynomials, high/low range (Sec. 2.1)
+# ---------------------------------------------------------------------------
+def nasa7(mech, T):
+    """cp/R, h/(RT), s/R for every species, shape [Ns, n].
+
+    Low-temperature coefficients are used iff T < T_mid (real part).
+    cp/R = a0 + a1 T + a2 T^2 + a3 T^3 + a4 T^4
+    h/RT = a0 + a1 T/2 + a2 T^2/3 + a3 T^3/4 + a4 T^4/5 + a5/T
+    s/R  = a0 ln T + a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a6
+    """
+    ns = mech.n_species
+    cp = np.empty((ns,) + np.shape(T), dtype=np.result_type(T, 1.0))
+    h = np.empty_like(cp)
+    s = np.empty_like(cp)
+    lnT = np.log(T)
+    for k in range(ns):
+        low = _re(T) < mech.T_mid[k]
+        a = [np.where(low, mech.nasa_low[k, j], mech.nasa_high[k, j]) for j in range(7)]
+        cp[k] = a[0] + a[1] * T + a[2] * T ** 2 + a[3] * T ** 3 + a[4] * T ** 4
+        h[k] = a[0] + a[1] * T / 2 + a[2] * T ** 2 / 3 + a[3] * T ** 3 / 4 + a[4] * T ** 4 / 5 + a[5] / T
+        s[k] = a[0] * lnT + a[1] * T + a[2] * T ** 2 / 2 + a[3] * T ** 3 / 3 + a[4] * T ** 4 / 4 + a[6]
+    return cp, h, s
+
+
+# ---------------------------------------------------------------------------
+# reaction rates (Sec. 2.2: R_i, c_i; modified Arrhenius; falloff forms)
+# ---------------------------------------------------------------------------
+def arrhenius(A, beta, Ea, T):
+    """Modified Arrhenius k = A T^beta exp(-Ea / (R_cal T)), Ea in cal/mol."""
+    return A * T ** beta * np.exp(-Ea / (R_CAL * T))
+
+
+def net_stoich(mech):
+    """nu[k, i] = nu''_ki - nu'_ki as a dense integer matrix [Ns, Nr]."""
+    nu = np.zeros((mech.n_species, mech.n_reactions), dtype=np.int64)
+    for i in range(mech.n_reactions):
+        for k, v in mech.reactants(i):
+            nu[k, i] -= v
+        for k, v in mech.products(i):
+            nu[k, i] += v
+    return nu
+
+
+def third_body_alpha(mech, i):
+    """Dense efficiency vector alpha[k] of reaction i (default 1)."""
+    a = np.ones(mech.n_species)
+    for k, v in mech.efficiencies(i).items():
+        a[k] = v
+    return a
+
+
+def troe_F(mech, i, T, Pr):
+    """Troe broadening factor (Gilbert, Luther & Troe 1983)."""
+    a, T3, T1, T2 = mech.troe[i]
+    Fcent = (1 - a) * np.exp(-T / T3) + a * np.exp(-T / T1)
+    if mech.troe_n[i] == 4:
+        Fcent = Fcent + np.exp(-T2 / T)
+    lF = np.log10(Fcent)
+    c = -0.4 - 0.67 * lF
+    N = 0.75 - 1.27 * lF
+    x = np.log10(Pr)
+    f1 = (x + c) / (N - 0.14 * (x + c))
+    return 10.0 ** (lF / (1 + f1 * f1))
+
+
+def sri_F(mech, i, T, Pr):
+    """SRI broadening factor (Stewart, Larson & Golden 1989)."""
+    a, b, c, d, e = mech.sri[i]
+    x = np.log10(Pr)
+    X = 1.0 / (1.0 + x * x)
+    return d * (a * np.exp(-b / T) + np.exp(-T / c)) ** X * T ** e
+
+
+def rates(mech, mode, phi, param, A=None, beta=None, Ea=None):
+    """All intermediate quantities of the source-term evaluation.
+
+    Returns a dict with T, V, P, C, Ctot, cp, h, s (NASA-7 forms), kf, kr,
+    c (pressure modification), Rf = kf prod C^nu', Rr = kr prod C^nu'',
+    qf = c Rf, qr = c Rr, q = qf - qr, wdot [Ns, n].
+
+    A, beta, Ea optionally override the high-pressure (or only) Arrhenius
+    parameters (used to differentiate with respect to them).
+    """
+    A = mech.A if A is None else A
+    beta = mech.beta if beta is None else beta
+    Ea = mech.Ea if Ea is None else Ea
+    T, V, P, C, Ctot = concentrations(mech, mode, phi, param)
+    cp, h, s = nasa7(mech, T)
+    g = h - s                                   # g/RT
+    nu = net_stoich(mech)
+    nr, ns = mech.n_reactions, mech.n_species
+    shape = (nr,) + np.shape(T)
+    dt = np.result_type(C, A, beta, Ea)
+    kf = np.empty(shape, dtype=dt)
+    kr = np.empty(shape, dtype=dt)
+    cmod = np.empty(shape, dtype=dt)
+    Rf = np.empty(shape, dtype=dt)
+    Rr = np.empty(shape, dtype=dt)
+    for i in range(nr):
+        kf[i] = arrhenius(A[i], beta[i], Ea[i], T)
+        if mech.reversible[i]:
+            dg = sum(nu[k, i] * g[k] for k in range(ns) if nu[k, i] != 0)
+            dn = float(nu[:, i].sum())
+            Kc = np.exp(-dg) * (P_ATM / (R * T)) ** dn
+            kr[i] = kf[i] / Kc
+        else:
+            kr[i] = 0.0
+        kind = mech.kind[i]
+        if kind == ELEMENTARY:
+            cmod[i] = 1.0
+        else:
+            M = third_body_alpha(mech, i) @ C.reshape(ns, -1)
+            M = M.reshape(np.shape(T))
+            if kind == THIRD_BODY:
+                cmod[i] = M
+            else:
+                k0 = arrhenius(mech.A0[i], mech.beta0[i], mech.Ea0[i], T)
+                Pr = k0 * M / kf[i]
+                if kind == LINDEMANN:
+                    F = 1.0
+                elif kind == TROE:
+                    F = troe_F(mech, i, T, Pr)
+                else:
+                    F = sri_F(mech, i, T, Pr)
+                cmod[i] = Pr / (1 + Pr) * F
+        fwd = kf[i]
+        for k, v in mech.reactants(i):
+            fwd = fwd * C[k] ** v
+        rev = kr[i]
+        for k, v in mech.products(i):
+            rev = rev * C[k] ** v
+        Rf[i], Rr[i] = fwd, rev
+    qf = cmod * Rf
+    qr = cmod * Rr
+    q = qf - qr
+    wdot = np.zeros((ns,) + np.shape(T), dtype=dt)
+    for i in range(nr):
+        for k in range(ns):
+            if nu[k, i] != 0:
+                wdot[k] = wdot[k] + nu[k, i] * q[i]
+    return dict(T=T, V=V, P=P, C=C, Ctot=Ctot, cp=cp, h=h, s=s, kf=kf, kr=kr, c=cmod,
+                Rf=Rf, Rr=Rr, qf=qf, qr=qr, q=q, wdot=wdot, nu=nu)
+
+
+def source_terms_from_rates(mech, mode, r):
+    """f = [dT/dt, dS/dt, dn_0/dt .. dn_{Ns-2}/dt] (Sec. 2.2).
+
+    CONP: dT/dt = -sum_k H_k wdot_k / sum_k C_k Cp_k,
+          dV/dt = V dT/dt / T + (R T V / P) sum_{k<Ns-1} (1 - W_k/W_Ns) wdot_k
+    CONV: dT/dt = -sum_k U_k wdot_k / sum_k C_k Cv_k,
+          dP/dt = P dT/dt / T + R T sum_{k<Ns-1} (1 - W_k/W_Ns) wdot_k
+    dn_k/dt = V wdot_k.  Sums over k run over all species, bath gas included.
+    """
+    ns = mech.n_species
+    T, V, P, C, wdot = r["T"], r["V"], r["P"], r["C"], r["wdot"]
+    if mode == CONP:
+        E = R * T * r["h"]             # molar enthalpy H_k
+        Cx = R * r["cp"]               # molar Cp_k
+    else:
+        E = R * T * (r["h"] - 1.0)     # molar internal energy U_k = H_k - R T
+        Cx = R * (r["cp"] - 1.0)       # molar Cv_k = Cp_k - R
+    num = sum(E[k] * wdot[k] for k in range(ns))
+    den = sum(C[k] * Cx[k] for k in range(ns))
+    Tdot = -num / den
+    Om = sum((1.0 - mech.W[k] / mech.W[ns - 1]) * wdot[k] for k in range(ns - 1))
+    f = np.empty((ns + 1,) + np.shape(T), dtype=wdot.dtype)
+    f[0] = Tdot
+    if mode == CONP:
+        f[1] = V * Tdot / T + (R * T * V / P) * Om
+    else:
+        f[1] = P * Tdot / T + R * T * Om
+    for k in range(ns - 1):
+        f[2 + k] = V * wdot[k]
+    return f, dict(E=E, Cx=Cx, num=num, den=den, Om=Om)
+
+
+def source_terms(mech, mode, phi, param):
+    """dPhi/dt for every state: array [Ns+1, n] (Sec. 2.2)."""
+    r = rates(mech, mode, phi, param)
+    return source_terms_from_rates(mech, mode, r)[0]
+
+
+# ---------------------------------------------------------------------------
+# Jacobian by complex-step differentiation (definition J_ij = df_i/dPhi_j)
+# ---------------------------------------------------------------------------
+def _cs_step(x):
+    return 1e-30 * np.maximum(np.abs(x), 1.0)
+
+
+def jacobian(mech, mode, phi, param, with_parts=False):
+    """Dense Jacobian [Ns+1, Ns+1, n] of f with P (CONP) or V (CONV) fixed.
+
+    Column j is Im f(Phi + i h e_j) / h with h = 1e-30 max(|Phi_j|, 1):
+    complex-step differentiation, which carries no subtractive cancellation
+    and equals the analytic derivative to rounding (the NASA-7 range choice
+    follows the real part of T).
+    With with_parts=True also returns the complex-step derivatives of the
+    forward/reverse parts (qf, qr), of the energy-equation denominator and the
+    values needed to bound rounding of a correct FP64 implementation.
+    """
+    N = mech.n_species + 1
+    n = phi.shape[1]
+    J = np.empty((N, N, n))
+    parts = dict(dqf=np.empty((mech.n_reactions, N, n)), dqr=np.empty((mech.n_reactions, N, n)),
+                 dden=np.empty((N, n)))
+    for j in range(N):
+        ph = phi.astype(np.complex128)
+        hj = _cs_step(phi[j])
+        ph[j] = ph[j] + 1j * hj
+        r = rates(mech, mode, ph, param.astype(np.complex128))
+        f, aux = source_terms_from_rates(mech, mode, r)
+        J[:, j] = f.imag / hj
+        if with_parts:
+            parts["dqf"][:, j] = r["qf"].imag / hj
+            parts["dqr"][:, j] = r["qr"].imag / hj
+            parts["dden"][j] = aux["den"].imag / hj
+    if with_parts:
+        return J, parts
+    return J
+
+
+# ---------------------------------------------------------------------------
+# rounding envelopes for a conditioning-aware comparison (Sec. 3.2: net rates
+# of progress lose accuracy where forward and reverse rates nearly cancel)
+# ---------------------------------------------------------------------------
+def source_term_envelope(mech, mode, phi, param):
+    """Absolute envelope env[Ns+1, n]: the sum of magnitudes of the terms that
+    make up each source term, so that a correct FP64 evaluation differs from
+    another by at most a small multiple of u * env."""
+    r = rates(mech, mode, phi, param)
+    f, aux = source_terms_from_rates(mech, mode, r)
+    ns = mech.n_species
+    nu = r["nu"]
+    ew = np.zeros_like(r["wdot"])
+    for i in range(mech.n_reactions):
+        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
+        for k in range(ns):
+            if nu[k, i] != 0:
+                ew[k] += abs(nu[k, i]) * t
+    T, V, P = r["T"], r["V"], r["P"]
+    den = np.abs(aux["den"])
+    eT = sum(np.abs(aux["E"][k]) * ew[k] for k in range(ns)) / den
+    eO = sum(abs(1.0 - mech.W[k] / mech.W[ns - 1]) * ew[k] for k in range(ns - 1))
+    env = np.empty_like(f)
+    env[0] = eT + np.abs(f[0])
+    if mode == CONP:
+        env[1] = V * env[0] / T + (R * T * V / P) * eO
+    else:
+        env[1] = P * env[0] / T + R * T * eO
+    for k in range(ns - 1):
+        env[2 + k] = V * ew[k]
+    return f, np.maximum(env, np.abs(f))
+
+
+def jacobian_envelope(mech, mode, phi, param):
+    """Jacobian J [N, N, n] and an absolute envelope of equal shape.
+
+    Species rows: V sum_i |nu_ki| (|d qf_i/dPhi_j| + |d qr_i/dPhi_j|).
+    Energy / state rows follow the structure of the source terms above.
+    """
+    J, parts = jacobian(mech, mode, phi, param, with_parts=True)
+    r = rates(mech, mode, phi, param)
+    f, aux = source_terms_from_rates(mech, mode, r)
+    _, envf = source_term_envelope(mech, mode, phi, param)
+    ns, N = mech.n_species, mech.n_species + 1
+    nu = r["nu"]
+    T, V, P = r["T"], r["V"], r["P"]
+    ew = np.zeros((ns, N) + np.shape(T))
+    for i in range(mech.n_reactions):
+        t = np.abs(parts["dqf"][i]) + np.abs(parts["dqr"][i])
+        for k in range(ns):
+            if nu[k, i] != 0:
+                ew[k] += abs(nu[k, i]) * t
+    env = np.zeros_like(J)
+    wd_env = envf[2:] / V  # envelope of wdot_k for k < Ns-1
+    for k in range(ns - 1):
+        env[2 + k] = V * ew[k]
+        if mode == CONP:
+            env[2 + k, 1] += wd_env[k]
+    den = np.abs(aux["den"])
+    Tdot = f[0]
+    eT = sum(np.abs(aux["E"][k]) * ew[k] for k in range(ns))      # [N, n]
+    # d(E_k)/dT = Cx_k contributes sum_k Cx_k wdot_k to the T column
+    ew_all = np.zeros((ns,) + np.shape(T))
+    for i in range(mech.n_reactions):
+        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
+        for k in range(ns):
+            if nu[k, i] != 0:
+                ew_all[k] += abs(nu[k, i]) * t
+    eT[0] += sum(np.abs(aux["Cx"][k]) * ew_all[k] for k in range(ns))
+    eT += (np.abs(Tdot) + envf[0]) * np.abs(parts["dden"])
+    env[0] = eT / den
+    eO = sum(abs(1.0 - mech.W[k] / mech.W[ns - 1]) * ew[k] for k in range(ns - 1))
+    eO0 = sum(abs(1.0 - mech.W[k] / mech.W[ns - 1]) * ew_all[k] for k in range(ns - 1))
+    if mode == CONP:
+        env[1] = (V / T) * env[0] + (R * T * V / P) * eO
+        env[1, 0] += V / T ** 2 * (np.abs(Tdot) + envf[0]) + R * V / P * eO0
+        env[1, 1] += (np.abs(Tdot) + envf[0]) / T + R * T / P * eO0
+    else:
+        env[1] = (P / T) * env[0] + R * T * eO
+        env[1, 0] += P / T ** 2 * (np.abs(Tdot) + envf[0]) + R * eO0
+        env[1, 1] += (np.abs(Tdot) + envf[0]) / T
+    return J, np.maximum(env, np.abs(J))
+
+
+# ---------------------------------------------------------------------------
+# sparsity pattern (Sec. 3.3)
+# ---------------------------------------------------------------------------
+def dependence_set(mech, i):
+    """Species j < Ns-1 on which the rate of progress of reaction i depends.
+
+    Reactants; products if reversible; for third-body / falloff reactions the
+    species whose efficiency differs from the bath gas's; and every species
+    when the bath gas takes part in the rate (as a reactant, as a product of a
+    reversible reaction) or has a non-unit efficiency (Sec. 3.3).
+    """
+    ns = mech.n_species
+    bath = ns - 1
+    dep = set()
+    members = [k for k, _ in mech.reactants(i)]
+    if mech.reversible[i]:
+        members += [k for k, _ in mech.products(i)]
+    dep.update(k for k in members if k != bath)
+    dense = bath in members
+    if mech.kind[i] != ELEMENTARY:
+        a = third_body_alpha(mech, i)
+        dep.update(k for k in range(ns - 1) if a[k] != a[bath])
+        if a[bath] != 1.0:
+            dense = True
+    if dense:
+        dep.update(range(ns - 1))
+    return dep
+
+
+def sparsity_pattern(mech):
+    """Boolean mask [N, N] of the exact Jacobian's structural nonzeros.
+
+    Rows/columns 0 (T) and 1 (V or P) are dense and the diagonal is kept; a
+    species row k has column j when some reaction changes k (nu_ki != 0) and
+    its rate depends on j (Sec. 3.3).  Identical for CONP and CONV.
+    """
+    ns, N = mech.n_species, mech.n_species + 1
+    nu = net_stoich(mech)
+    mask = np.zeros((N, N), dtype=bool)
+    mask[0, :] = mask[1, :] = True
+    mask[:, 0] = mask[:, 1] = True
+    mask[np.arange(N), np.arange(N)] = True
+    for i in range(mech.n_reactions):
+        dep = dependence_set(mech, i)
+        for k in range(ns - 1):
+            if nu[k, i] != 0:
+                for j in dep:
+                    mask[2 + k, 2 + j] = True
+    return mask
+
+
+def csr_pattern(mech):
+    """(row_ptr [N+1], col_idx [nnz]) with columns ascending in each row."""
+    mask = sparsity_pattern(mech)
+    N = mask.shape[0]
+    row_ptr = np.zeros(N + 1, dtype=np.int32)
+    cols = []
+    for i in range(N):
+        c = [j for j in range(N) if mask[i, j]]
+        cols += c
+        row_ptr[i + 1] = row_ptr[i] + len(c)
+    return row_ptr, np.array(cols, dtype=np.int32)
+
+
+def csc_pattern(mech):
+    """(col_ptr [N+1], row_idx [nnz]) with rows ascending in each column."""
+    mask = sparsity_pattern(mech)
+    N = mask.shape[0]
+    col_ptr = np.zeros(N + 1, dtype=np.int32)
+    rows = []
+    for j in range(N):
+        r = [i for i in range(N) if mask[i, j]]
+        rows += r
+        col_ptr[j + 1] = col_ptr[j] + len(r)
+    return col_ptr, np.array(rows, dtype=np.int32)
+
+
+def dense_to_csr_values(mech, J):
+    """Values [nnz, n] of a dense Jacobian stack in CSR order."""
+    row_ptr, col = csr_pattern(mech)
+    rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+    return J[rows, col]
+
+
+def dense_to_csc_values(mech, J):
+    col_ptr, row = csc_pattern(mech)
+    cols = np.repeat(np.arange(len(col_ptr) - 1), np.diff(col_ptr))
+    return J[row, cols]

@@ -1,0 +1,147 @@
+"""Planted mistakes: each plausible slip in the oracle's formulas must make at
+least one pin fail.  The mistake is planted in a copy of the oracle's source
+on the CPU; the real oracle is untouched."""
+import importlib.util
+import math
+import os
+import types
+
+import numpy as np
+import pytest
+
+import synth
+from tests import tiny_mechs as tm
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "kinetics.py")
+U = 2.0 ** -53
+
+
+def mutant(old, new):
+    src = open(SRC).read()
+    assert old in src, old
+    mod = types.ModuleType("oracle_mutant")
+    exec(compile(src.replace(old, new, 1), "oracle_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def real():
+    return mutant("import numpy as np", "import numpy as np")
+
+
+# ---- compact pins (each returns True when the pin holds) -------------------
+def pin_equilibrium(K, mech):
+    rng = np.random.default_rng(1)
+    ns = mech.n_species
+    T = 1500.0
+    _, hrt, sr = K.nasa7(mech, np.array([T]))
+    g = (hrt - sr)[:, 0]
+    lc0 = math.log(101325.0 / (8314.46261815324 * T))
+    target = lc0 - rng.uniform(2.0, 8.0, ns)
+    target[-1] = lc0
+    w = np.ones(ns)
+    w[-1] = 100.0
+    lam, *_ = np.linalg.lstsq(mech.composition * w[:, None], (target + g) * w, rcond=None)
+    C = np.exp(mech.composition @ lam - g + lc0)
+    phi = np.concatenate([[T, 1.0], C[:-1]])[:, None]
+    par = np.array([8314.46261815324 * T * C.sum()])
+    r = K.rates(mech, 0, phi, par)
+    rev = mech.reversible
+    return bool(np.all(np.abs(r["Rf"][rev, 0] - r["Rr"][rev, 0]) <= 1e-9 * np.maximum(r["Rf"][rev, 0], r["Rr"][rev, 0])))
+
+
+def pin_thermo(K, mech):
+    T = np.array([700.0, 1500.0])
+    cp, hh, ss = K.nasa7(mech, T)
+    _, hc, sc = K.nasa7(mech, T + 1e-20j)
+    return bool(np.allclose(((T + 1e-20j) * hc).imag / 1e-20, cp, rtol=1e-12)
+                and np.allclose(sc.imag / 1e-20, cp / T, rtol=1e-12))
+
+
+def pin_conservation(K, mech, mode):
+    phi, par = synth.make_states(mech, 4, 3, mode)
+    f = K.source_terms(mech, mode, phi, par)
+    ns = mech.n_species
+    ok = True
+    for s in range(4):
+        def tot(ph):
+            T = ph[0]
+            V, P = (ph[1], par[s]) if mode == 0 else (par[s], ph[1])
+            n = list(ph[2:]) + [P * V / (8314.46261815324 * T) - sum(ph[2:])]
+            _, hrt, _ = K.nasa7(mech, T)
+            e = hrt if mode == 0 else hrt - 1.0
+            return (sum(n[k] * 8314.46261815324 * T * e[k] for k in range(ns)),
+                    sum(n[k] * mech.W[k] for k in range(ns)))
+        z = phi[:, s].astype(complex) + 1e-30j * f[:, s]
+        dE, dm = (x.imag / 1e-30 for x in tot(z))
+        E_scale = np.sum(np.abs(8314.46261815324 * phi[0, s] * np.abs(f[2:, s]))) * 1e3 + 1e-300
+        m_scale = np.sum(mech.W[:-1] * np.abs(f[2:, s])) + 1e-300
+        ok &= abs(dE) <= 1e-9 * E_scale and abs(dm) <= 1e-9 * m_scale
+    return bool(ok)
+
+
+def pin_single_rate(K):
+    m = tm.single(dict(reac=[(tm.H, 1), (tm.O2, 1)], prod=[(tm.HO2, 1)], A=7.0, rev=False))
+    T, P = 1500.0, 2.0e5
+    X = np.zeros(10)
+    X[tm.H], X[tm.O2], X[tm.HO2], X[tm.N2] = 0.1, 0.2, 0.05, 0.65
+    ntot = P / (8314.46261815324 * T)
+    phi = np.concatenate([[T, 1.0], X[:-1] * ntot])[:, None]
+    r = K.rates(m, 0, phi, np.array([P]))
+    q = 7.0 * (0.1 * ntot) * (0.2 * ntot)
+    return bool(abs(r["wdot"][tm.H, 0] + q) <= 1e-12 * q and abs(r["wdot"][tm.HO2, 0] - q) <= 1e-12 * q)
+
+
+def pin_third_body(K):
+    m = tm.single(dict(reac=[(tm.H, 2)], prod=[(tm.H2, 1)], A=2.0, rev=False, kind=synth.THIRD_BODY,
+                       eff={tm.H2O: 5.0, tm.N2: 0.5}))
+    P, T = 3e5, 1100.0
+    ntot = P / (8314.46261815324 * T)
+    phi = np.concatenate([[T, 1.0], np.full(9, 0.1 * ntot)])[:, None]
+    r = K.rates(m, 0, phi, np.array([P]))
+    return bool(abs(r["c"][0, 0] - 0.1 * ntot * (8 + 5.0 + 0.5)) <= 1e-12 * ntot)
+
+
+def pin_troe_center(K):
+    m = tm.single(dict(reac=[(tm.H, 1), (tm.O2, 1)], prod=[(tm.HO2, 1)], A=1e8, rev=False,
+                       kind=synth.TROE, A0=1.0, troe=(0.6, 200.0, 1500.0, 4000.0)))
+    T = 1200.0
+    Fc = 0.4 * math.exp(-T / 200.0) + 0.6 * math.exp(-T / 1500.0) + math.exp(-4000.0 / T)
+    F = K.troe_F(m, 0, np.array([T]), np.array([10 ** (0.4 + 0.67 * math.log10(Fc))]))[0]
+    return bool(abs(F - Fc) <= 1e-12 * Fc)
+
+
+def all_pins(K, mechs):
+    g = mechs("h2co13")
+    a = tm.all_kinds()
+    return dict(equilibrium=pin_equilibrium(K, g), thermo=pin_thermo(K, g),
+                cons_conp=pin_conservation(K, a, 0), cons_conv=pin_conservation(K, a, 1),
+                single=pin_single_rate(K), third_body=pin_third_body(K), troe=pin_troe_center(K))
+
+
+MUTATIONS = [
+    ("np.exp(-dg) * (P_ATM", "np.exp(dg) * (P_ATM"),
+    ("(P_ATM / (R * T)) ** dn", "(P_ATM / (R * T)) ** (-dn)"),
+    ("a[2] * T ** 2 / 3 + a[3]", "a[2] * T ** 2 / 2 + a[3]"),
+    ("s[k] = a[0] * lnT", "s[k] = a[0] * T"),
+    ("+ a[5] / T", "+ a[5] * T"),
+    ("(1.0 - mech.W[k] / mech.W[ns - 1]) * wdot[k]", "1.0 * wdot[k]"),
+    ("num = sum(E[k] * wdot[k] for k in range(ns))", "num = sum(E[k] * wdot[k] for k in range(ns - 1))"),
+    ("Cx = R * (r[\"cp\"] - 1.0)", "Cx = R * r[\"cp\"]"),
+    ("wdot[k] = wdot[k] + nu[k, i] * q[i]", "wdot[k] = wdot[k] - nu[k, i] * q[i]"),
+    ("a = np.ones(mech.n_species)", "a = np.zeros(mech.n_species)"),
+    ("C[ns - 1] = Ctot - acc", "C[ns - 1] = Ctot"),
+    ("c = -0.4 - 0.67 * lF", "c = -0.4 - 0.76 * lF"),
+    ("f[1] = V * Tdot / T + (R * T * V / P) * Om", "f[1] = V * Tdot / T + (R * V / P) * Om"),
+    ("f[1] = P * Tdot / T + R * T * Om", "f[1] = P * Tdot / T + R * Om"),
+]
+
+
+def test_real_oracle_passes_compact_pins(mechs):
+    res = all_pins(real(), mechs)
+    assert all(res.values()), res
+
+
+@pytest.mark.parametrize("old,new", MUTATIONS)
+def test_planted_mistake_is_caught(mechs, old, new):
+    res = all_pins(mutant(old, new), mechs)
+    assert not all(res.values()), f"mutation {old!r} -> {new!r} escaped all pins: {res}"

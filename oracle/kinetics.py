@@ -144,7 +144,7 @@ def sri_F(mech, i, T, Pr):
     return d * (a * np.exp(-b / T) + np.exp(-T / c)) ** X * T ** e
 
 
-def rates(mech, mode, phi, param, A=None, beta=None, Ea=None):
+def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
     """All intermediate quantities of the source-term evaluation.
 
     Returns a dict with T, V, P, C, Ctot, cp, h, s (NASA-7 forms), kf, kr,
@@ -152,12 +152,16 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None):
     qf = c Rf, qr = c Rr, q = qf - qr, wdot [Ns, n].
 
     A, beta, Ea optionally override the high-pressure (or only) Arrhenius
-    parameters (used to differentiate with respect to them).
+    parameters (used to differentiate with respect to them); dC is added to
+    the concentrations after they are formed (used to differentiate with
+    respect to a single concentration).
     """
     A = mech.A if A is None else A
     beta = mech.beta if beta is None else beta
     Ea = mech.Ea if Ea is None else Ea
     T, V, P, C, Ctot = concentrations(mech, mode, phi, param)
+    if dC is not None:
+        C = C + dC
     cp, h, s = nasa7(mech, T)
     g = h - s                                   # g/RT
     nu = net_stoich(mech)
@@ -195,7 +199,10 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None):
                     F = troe_F(mech, i, T, Pr)
                 else:
                     F = sri_F(mech, i, T, Pr)
-                cmod[i] = Pr / (1 + Pr) * F
+                # Pr/(1+Pr) written as 1/(1+1/Pr): the same function, but its
+                # complex-step derivative avoids the cancellation
+                # (1+Pr) dPr - Pr dPr that loses digits for large Pr
+                cmod[i] = F / (1 + 1 / Pr)
         fwd = kf[i]
         for k, v in mech.reactants(i):
             fwd = fwd * C[k] ** v
@@ -328,24 +335,52 @@ def source_term_envelope(mech, mode, phi, param):
 def jacobian_envelope(mech, mode, phi, param):
     """Jacobian J [N, N, n] and an absolute envelope of equal shape.
 
-    Species rows: V sum_i |nu_ki| (|d qf_i/dPhi_j| + |d qr_i/dPhi_j|).
-    Energy / state rows follow the structure of the source terms above.
+    Per reaction, the envelope of d q_i / d Phi_j sums the magnitudes of the
+    forward and reverse parts and of the paths through the bath-gas
+    concentration (which can cancel a species' own term):
+      species columns: (|dqf/dC_j| + |dqr/dC_j| + |dqf/dC_b| + |dqr/dC_b|) / V
+      T, S columns:    |dqf/dPhi| + |dqr/dPhi| + (|dqf/dC_b| + |dqr/dC_b|) |dC_b/dPhi|
+                       (+ sum_k (|dqf/dC_k| + |dqr/dC_k|) C_k / V for V in CONP)
+    Species rows combine these with |nu_ki|; energy / state rows follow the
+    structure of the source terms.
     """
     J, parts = jacobian(mech, mode, phi, param, with_parts=True)
     r = rates(mech, mode, phi, param)
     f, aux = source_terms_from_rates(mech, mode, r)
     _, envf = source_term_envelope(mech, mode, phi, param)
-    ns, N = mech.n_species, mech.n_species + 1
+    ns, N, nr = mech.n_species, mech.n_species + 1, mech.n_reactions
     nu = r["nu"]
-    T, V, P = r["T"], r["V"], r["P"]
-    ew = np.zeros((ns, N) + np.shape(T))
-    for i in range(mech.n_reactions):
-        t = np.abs(parts["dqf"][i]) + np.abs(parts["dqr"][i])
+    T, V, P, C, Ctot = r["T"], r["V"], r["P"], r["C"], r["Ctot"]
+    shape = np.shape(T)
+    # complex-step derivatives of the forward / reverse parts w.r.t. each C_k
+    dC_mag = np.empty((nr, ns) + shape)
+    for k in range(ns):
+        hk = 1e-30 * np.maximum(np.abs(C[k]), 1e-200)
+        dC = np.zeros((ns,) + shape, dtype=np.complex128)
+        dC[k] = 1j * hk
+        rk = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128), dC=dC)
+        dC_mag[:, k] = (np.abs(rk["qf"].imag) + np.abs(rk["qr"].imag)) / hk
+    bath = dC_mag[:, ns - 1]                                   # [Nr, n]
+    eq = np.empty((nr, N) + shape)                             # per-reaction envelope of dq_i/dPhi_j
+    eq[:, 0] = np.abs(parts["dqf"][:, 0]) + np.abs(parts["dqr"][:, 0]) + bath * Ctot / T
+    if mode == CONP:
+        dCb_S = (Ctot - C[ns - 1]) / V
+        eq[:, 1] = np.abs(parts["dqf"][:, 1]) + np.abs(parts["dqr"][:, 1]) + bath * np.abs(dCb_S)
+        eq[:, 1] += sum(dC_mag[:, k] * np.abs(C[k]) for k in range(ns - 1)) / V
+    else:
+        eq[:, 1] = np.abs(parts["dqf"][:, 1]) + np.abs(parts["dqr"][:, 1]) + bath * Ctot / P
+    for j in range(ns - 1):
+        eq[:, 2 + j] = (dC_mag[:, j] + bath) / V
+    ew = np.zeros((ns, N) + shape)
+    ew_all = np.zeros((ns,) + shape)
+    for i in range(nr):
+        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
         for k in range(ns):
             if nu[k, i] != 0:
-                ew[k] += abs(nu[k, i]) * t
+                ew[k] += abs(nu[k, i]) * eq[i]
+                ew_all[k] += abs(nu[k, i]) * t
     env = np.zeros_like(J)
-    wd_env = envf[2:] / V  # envelope of wdot_k for k < Ns-1
+    wd_env = envf[2:] / V
     for k in range(ns - 1):
         env[2 + k] = V * ew[k]
         if mode == CONP:
@@ -353,13 +388,6 @@ def jacobian_envelope(mech, mode, phi, param):
     den = np.abs(aux["den"])
     Tdot = f[0]
     eT = sum(np.abs(aux["E"][k]) * ew[k] for k in range(ns))      # [N, n]
-    # d(E_k)/dT = Cx_k contributes sum_k Cx_k wdot_k to the T column
-    ew_all = np.zeros((ns,) + np.shape(T))
-    for i in range(mech.n_reactions):
-        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
-        for k in range(ns):
-            if nu[k, i] != 0:
-                ew_all[k] += abs(nu[k, i]) * t
     eT[0] += sum(np.abs(aux["Cx"][k]) * ew_all[k] for k in range(ns))
     eT += (np.abs(Tdot) + envf[0]) * np.abs(parts["dden"])
     env[0] = eT / den

@@ -1,0 +1,334 @@
+"""Benchmark: Jacobian + source-term evaluations per second on GB300.
+
+A step is one pass of the whole hot path over one batch: concentrations,
+NASA-7 thermo, forward/reverse rate constants, pressure modification,
+rates of progress, production rates, dT/dt and dV/dt, and the exact sparse
+(CSR) Jacobian, all in one kernel launch (k_jacobian with source-term
+output), for the 53-species / 325-reaction synthetic mechanism and 1,048,576
+CONP states resident in HBM (inputs and outputs larger than L2).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank evaluates its own batch (replicas; weak
+scaling) with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian & source-term evals/s (states/s) at FP64 tol vs oracle; roofline %"
+UNIT = "states/s"
+WORKLOAD = "gri53_1m"
+
+# FP64 cost of CUDA's exp / log / divide in DFMA issue slots, measured on this
+# GB300 (dfma 505 G/s, exp 31.5 G/s, log 16.7 G/s, div 88.9 G/s).
+W_EXP, W_LOG, W_DIV = 16.0, 30.2, 5.7
+# FP64 peak derived from unit counts and clock: 2 DFMA / clock / SM
+# (1.25 TFLOP/s nominal for GB300) x 152 SMs x 2070 MHz.
+FP64_DFMA_PER_CLK_SM = 2.0
+
+
+def fp64_work_per_state(m, jacobian=True):
+    """Algorithmic FP64 work per state in DFMA-equivalents."""
+    import synth
+    ns, nr = m.n_species, m.n_reactions
+    w = 0.0
+    w += (ns - 1) * W_DIV + (ns - 1) + 3 + W_DIV       # concentrations, C_tot, bath gas
+    w += W_LOG + W_DIV + 15 * ns + ns                   # ln T, 1/T, NASA-7 cp/h/s/g, denominator
+    for i in range(nr):
+        r, p = m.reactants(i), m.products(i)
+        nre, npr = len(r), len(p)
+        sre, spr = sum(v for _, v in r), sum(v for _, v in p)
+        kind = int(m.kind[i])
+        w += 2 + W_EXP + (sre - 1) + 1                  # kf and forward product
+        if m.reversible[i]:
+            w += (nre + npr) + 2 + W_EXP + (spr - 1) + 1
+        if kind != synth.ELEMENTARY:
+            w += len(m.efficiencies(i))
+        if kind in (synth.LINDEMANN, synth.TROE, synth.SRI):
+            w += 2 + W_EXP + 1 + W_DIV + 2             # k0/kinf, Pr, Pr/(1+Pr) F
+            if kind == synth.TROE:
+                w += (3 if m.troe_n[i] == 4 else 2) * W_EXP + 2 * W_LOG + W_EXP + W_DIV * 2 + 12
+            elif kind == synth.SRI:
+                w += 3 * W_EXP + 2 * W_LOG + W_DIV + 8
+        w += 2 + (nre + npr)                            # q, production-rate scatter
+        if jacobian:
+            w += 2 + nre + (nre + npr)                  # dln kf/dT, dRf/dC, sum nu h
+            if m.reversible[i]:
+                w += 3 + npr
+            if kind == synth.THIRD_BODY:
+                w += 4
+            elif kind != synth.ELEMENTARY:
+                w += 2 + 12 + W_DIV
+                if kind == synth.TROE:
+                    w += 16 + W_DIV
+                elif kind == synth.SRI:
+                    w += 10 + W_DIV
+            w += 4 + (nre + npr) + 4 + 3 + 4          # dR/dT, dR/dS, dq/dT, dq/dS, dE, accumulators
+            rows = sum(1 for k in range(ns - 1) if (sum(v for kk, v in p if kk == k) - sum(v for kk, v in r if kk == k)) != 0)
+            slots = nre + (npr if m.reversible[i] else 0) + (len(m.efficiencies(i)) if kind else 0)
+            w += 2 * rows + slots * (1 + rows + 2)     # products feeding the L2 reductions
+    w += ns + 2 * (ns - 1) + W_DIV + 10                 # energy and state equations
+    if jacobian:
+        w += (ns + 1) * (12 + 2 * W_DIV) + 2 * ns + 4 * W_DIV   # T and S rows
+    return w
+
+
+def sample_clocks_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(handle, path, gpu_index):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(m, mode, n_sample, seed):
+    """The CPU oracle as it stands on a bounded sample (source terms + complex-step Jacobian)."""
+    import oracle
+    import synth
+    phi, par = synth.make_states(m, n_sample, seed, mode)
+    t0 = time.perf_counter()
+    oracle.source_terms(m, mode, phi, par)
+    J = oracle.jacobian(m, mode, phi, par)
+    oracle.dense_to_csr_values(m, J)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args, rank, world):
+    import synth
+    if rank != 0:
+        return
+    m = synth.make_mechanism("gri53")
+    n_sample = 64
+    times = []
+    for _ in range(args.warmup):
+        oracle_baseline(m, synth.CONP, 8, 7)
+    for s in range(args.steps):
+        _, dt = oracle_baseline(m, synth.CONP, n_sample, 2018 + 2 + s)
+        times.append(dt)
+    v = n_sample * args.steps / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mechanism": "synthetic 53 species / 325 reactions", "mode": "CONP",
+                   "output": "source terms + CSR Jacobian", "sample_states_per_step": n_sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample} states per step of the {WORKLOAD} workload (numpy, complex-step Jacobian)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1048576, help="states per GPU")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_1809_01029_gb300 as pj
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    pj.load_library()
+    m = synth.make_mechanism("gri53")
+    h = pj.pj_mech_create(m)
+    n = args.n
+    mode = synth.CONP
+    phi_h, par_h = synth.make_states(m, n, 2018 + 2 + 1000 * rank, mode)
+    dev = torch.device("cuda", local)
+    phi = torch.from_numpy(phi_h).to(dev)
+    par = torch.from_numpy(par_h).to(dev)
+    vals = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    dphi = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    wb = h.workspace_size(pj.PJ_OP_JACOBIAN, n)
+    work = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    wbs = h.workspace_size(pj.PJ_OP_SOURCE, n)
+    work_s = torch.empty(max(wbs, 1), dtype=torch.uint8, device=dev)
+
+    def step():
+        pj.pj_eval_jacobian_sparse(h, mode, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk = sample_clocks_start(clk_path)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sample_clocks_stop(clk, clk_path, local)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n * world / (ms_max * 1e-3)
+    assert int(status.item()) == 0, "invalid states in the benchmark batch"
+
+    # roofline of the (single) kernel of the step: FP64 pipe
+    fp64_work = fp64_work_per_state(m, jacobian=True)
+    achieved = fp64_work * n / (ms * 1e-3) / 1e9     # G DFMA-equivalent / s
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_jacobian<CONP,CSR>", "work_per_state": fp64_work,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
+
+    variants = {}
+    if not args.no_variants:
+        def timeit(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+        for md, nm in ((synth.CONP, "conp"), (synth.CONV, "conv")):
+            t_src = timeit(lambda: pj.pj_eval_source_terms(h, md, n, par, phi, n, dphi, status, work_s, wbs, stream))
+            variants[f"source_{nm}"] = n / (t_src * 1e-3)
+        variants["jacobian_csc_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
+            h, mode, pj.PJ_CSC, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
+        variants["jacobian_csr_conv"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
+            h, synth.CONV, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
+        del vals
+        torch.cuda.empty_cache()
+        N1 = m.n_species + 1
+        jd = torch.empty((N1 * N1, n), dtype=torch.float64, device=dev)
+        variants["jacobian_dense_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_dense(
+            h, mode, n, par, phi, n, jd, dphi, status, work, wb, stream)) * 1e-3)
+        del jd
+        torch.cuda.empty_cache()
+        vals = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+
+    e2e = None
+    if not args.no_e2e:
+        # the same step through the public API with HOST buffers: H2D of the
+        # states, the kernel, D2H of the Jacobian values and source terms
+        phi_pin = torch.from_numpy(phi_h).pin_memory()
+        par_pin = torch.from_numpy(par_h).pin_memory()
+        vals_pin = torch.empty((h.nnz, n), dtype=torch.float64).pin_memory()
+        dphi_pin = torch.empty((m.n_species + 1, n), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            phi.copy_(phi_pin, non_blocking=True)
+            par.copy_(par_pin, non_blocking=True)
+            step()
+            vals_pin.copy_(vals, non_blocking=True)
+            dphi_pin.copy_(dphi, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(k):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / k
+        e2e = {"value": n * world / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(phi_pin.numel() * 8 + par_pin.numel() * 8),
+               "d2h_bytes_per_step": int(vals_pin.numel() * 8 + dphi_pin.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt = oracle_baseline(m, mode, 48, 2018 + 2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"48 states of the {WORKLOAD} workload: numpy source terms + complex-step CSR Jacobian "
+                         f"({dt:.1f} s)"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mechanism": "synthetic 53 species / 325 reactions (seed 1811)",
+                       "states_per_gpu": n, "mode": "CONP", "output": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
+                       "l2": "inputs and outputs larger than L2 (%.1f GB per step)" % ((h.nnz + 2 * (m.n_species + 1)) * n * 8 / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps, "variants": variants}))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

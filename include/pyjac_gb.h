@@ -1,0 +1,196 @@
+/*
+ * pyjac_gb.h -- C ABI of the GB300 library for thermochemical source terms
+ * and analytical chemical-kinetic Jacobians (Curtis, Niemeyer & Sung,
+ * "Using SIMD and SIMT vectorization to evaluate sparse chemical kinetic
+ * Jacobian matrices and thermochemical source terms", arXiv:1809.01029).
+ *
+ * Conventions (every entry point):
+ *  - Returns PJ_OK (0) or a PJ_ERR_* code; pj_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.  No
+ *    C++ exception crosses this boundary.
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (e.g. PyTorch
+ *    tensors); the library never frees them and never synchronises the
+ *    stream.  Pointers named h_* are host pointers.  `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - State layout is structure-of-arrays (the paper's "F" ordering for
+ *    shallow GPU vectorisation, Sec. 2.1): element v of state s is
+ *    phi[v*ld + s] for v in [0, Ns] and s in [0, n), with ld >= n.  The state
+ *    vector is Phi = [T, S, n_0 .. n_{Ns-2}] (Sec. 2.2): T in K; S = V [m^3]
+ *    under constant pressure (PJ_CONP, P is the per-state parameter) or
+ *    S = P [Pa] under constant volume (PJ_CONV, V is the parameter); n_k in
+ *    kmol.  Species Ns-1 (the bath gas) is implicit through P V = n R T.
+ *  - param[s] is P [Pa] (CONP) or V [m^3] (CONV), one per state.
+ *  - Outputs use the same layout with the same ld: source terms
+ *    dphi[v*ld + s]; sparse Jacobian values vals[e*ld + s] for e in [0, nnz)
+ *    in the order of pj_sparsity(); dense Jacobian jac[(i*(Ns+1)+j)*ld + s]
+ *    with i the source term (row) and j the state variable (column),
+ *    Sec. 2.2 "Jacobian arrangement".
+ *  - Units are SI with kmol: R = 8314.46261815324 J/(kmol K), activation
+ *    energies in cal/mol (R_cal = 1.98720425864083 cal/(mol K)), standard
+ *    pressure 101325 Pa.
+ *  - Invalid states (T, V or P <= 0, any non-finite input, or a bath-gas
+ *    concentration below -1e-12 of the total) get NaN outputs; if `d_status` (a device int)
+ *    is non-NULL the number of such states is added to it atomically.
+ *    Kernels never trap.
+ *  - A mechanism handle is immutable after creation and may be used
+ *    concurrently from several host threads on different streams.  Its
+ *    constants live on the device that was current at creation; evaluation
+ *    calls must run with that device current (PJ_ERR_ARG otherwise).
+ */
+#ifndef PYJAC_GB_H
+#define PYJAC_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PJ_OK 0
+#define PJ_ERR_ARG 1          /* invalid argument (null pointer, ld < n, bad enum, ...) */
+#define PJ_ERR_MECH 2         /* malformed mechanism (file or arrays) */
+#define PJ_ERR_CUDA 3         /* a CUDA runtime call or launch failed */
+#define PJ_ERR_NOMEM 4        /* host or device allocation failed / workspace too small */
+#define PJ_ERR_UNSUPPORTED 5  /* valid request this build does not handle */
+#define PJ_ERR_TIMEOUT 6      /* a bounded device-side wait gave up */
+
+/* evaluation assumption (Sec. 2.2) */
+#define PJ_CONP 0
+#define PJ_CONV 1
+
+/* Jacobian storage (Sec. 3.3: compressed row / column storage) */
+#define PJ_CSR 0
+#define PJ_CSC 1
+#define PJ_DENSE 2
+
+/* reaction kinds */
+#define PJ_ELEMENTARY 0
+#define PJ_THIRD_BODY 1
+#define PJ_LINDEMANN 2
+#define PJ_TROE 3
+#define PJ_SRI 4
+
+#define PJ_MAX_SP 4 /* distinct species per reaction side */
+
+typedef struct pj_mech pj_mech;
+
+/* Mechanism description: plain arrays, 0-based species indices, the last
+ * species is the bath gas.  All arrays are host memory and are copied; the
+ * caller keeps ownership.
+ *   W[Ns]                 molecular weights, kg/kmol
+ *   T_mid[Ns]             NASA-7 range switch: low coefficients iff T < T_mid
+ *   nasa_low[Ns*7], nasa_high[Ns*7]  a0..a6 (cp/R = a0 + a1 T + .. + a4 T^4,
+ *                         h/RT adds a5/T, s/R adds a6)
+ *   kind[Nr]              PJ_ELEMENTARY .. PJ_SRI
+ *   reversible[Nr]        0/1; reverse rate from the equilibrium constant
+ *   reac_sp/reac_nu[Nr*PJ_MAX_SP], prod_sp/prod_nu[...]: species (-1 pads)
+ *                         and positive integer stoichiometric coefficients
+ *   A, beta, Ea [Nr]      modified Arrhenius k = A T^beta exp(-Ea/(R_cal T));
+ *                         the high-pressure limit for falloff reactions
+ *   A0, beta0, Ea0 [Nr]   low-pressure limit (falloff kinds only)
+ *   troe[Nr*4], troe_n[Nr]  a, T3, T1, T2 and the number of parameters (3|4)
+ *   sri[Nr*5]             a, b, c, d, e
+ *   eff_ptr[Nr+1], eff_sp[], eff_val[]  non-default third-body efficiencies
+ *                         (CSR by reaction; default efficiency is 1)
+ */
+typedef struct {
+  int32_t n_species, n_reactions;
+  const double* W;
+  const double* T_mid;
+  const double* nasa_low;
+  const double* nasa_high;
+  const int32_t* kind;
+  const int32_t* reversible;
+  const int32_t* reac_sp;
+  const int32_t* reac_nu;
+  const int32_t* prod_sp;
+  const int32_t* prod_nu;
+  const double* A;
+  const double* beta;
+  const double* Ea;
+  const double* A0;
+  const double* beta0;
+  const double* Ea0;
+  const double* troe;
+  const int32_t* troe_n;
+  const double* sri;
+  const int32_t* eff_ptr;
+  const int32_t* eff_sp;
+  const double* eff_val;
+} pj_mech_desc;
+
+/* Thread-local message describing the last error on this thread. */
+const char* pj_last_error(void);
+
+/* Library version string. */
+const char* pj_version(void);
+
+/* Build a mechanism from arrays (copied), pack its constants for the
+ * kernels, build the fixed sparsity pattern (Sec. 3.3) and upload both to the
+ * current device.  *out receives a handle to release with pj_mech_free().
+ * With no CUDA device present the handle is host-only: pj_mech_info and
+ * pj_sparsity work, evaluation calls return PJ_ERR_CUDA.
+ * Errors: PJ_ERR_ARG (null), PJ_ERR_MECH (index out of range, non-positive
+ * A, bad kind, ...), PJ_ERR_CUDA / PJ_ERR_NOMEM (upload). */
+int pj_mech_create(const pj_mech_desc* desc, pj_mech** out);
+
+/* Same from a PJMECH text file (format documented in synth/mechfile.py:
+ * one record per species and per reaction). */
+int pj_mech_load(const char* path, pj_mech** out);
+
+/* Release the handle and its device constants.  NULL is accepted. */
+int pj_mech_free(pj_mech* mech);
+
+/* Sizes: species, reactions, and nonzeros of the sparse Jacobian. */
+int pj_mech_info(const pj_mech* mech, int32_t* n_species, int32_t* n_reactions, int32_t* nnz);
+
+/* Sparsity pattern of the exact Jacobian (Sec. 3.3), identical for CONP and
+ * CONV: rows/columns of T and S dense, diagonal kept, species row k has
+ * column j when a reaction that changes k has a rate depending on j (its
+ * reactants, its products if reversible, species whose third-body efficiency
+ * differs from the bath gas's, or every species when the bath gas takes part
+ * in the rate).  fmt = PJ_CSR: h_ptr[Ns+2] row pointers, h_idx[nnz] column
+ * indices ascending per row; PJ_CSC: column pointers / row indices. */
+int pj_sparsity(const pj_mech* mech, int fmt, int32_t* h_ptr, int32_t* h_idx);
+
+/* Source terms f = dPhi/dt (Sec. 2.2: molar source terms dn_k/dt = V wdot_k
+ * with wdot_k = sum_i nu_ki R_i c_i; dT/dt from species enthalpies (CONP) or
+ * internal energies (CONV); dV/dt or dP/dt from the ideal-gas law with the
+ * bath gas closing the mass balance) for n states.  d_work / work_bytes: device
+ * scratch of at least pj_workspace_size(PJ_OP_SOURCE) bytes (NULL when 0);
+ * PJ_ERR_NOMEM if it is too small. */
+int pj_eval_source_terms(const pj_mech* mech, int mode, int64_t n, const double* d_param,
+                         const double* d_phi, int64_t ld, double* d_dphi, int* d_status,
+                         void* d_work, size_t work_bytes, void* stream);
+
+/* Exact analytical Jacobian J_ij = d f_i / d Phi_j (Sec. 2.2 "Jacobian
+ * arrangement"; sparse storage Sec. 3.3) in CSR (fmt = PJ_CSR) or CSC
+ * (PJ_CSC) value order: d_vals[e*ld + s].  d_dphi, if non-NULL, also
+ * receives the source terms.  d_work must point to pj_workspace_size() bytes
+ * of device memory (may be NULL when that size is 0). */
+int pj_eval_jacobian_sparse(const pj_mech* mech, int mode, int fmt, int64_t n,
+                            const double* d_param, const double* d_phi, int64_t ld,
+                            double* d_vals, double* d_dphi, int* d_status,
+                            void* d_work, size_t work_bytes, void* stream);
+
+/* Same, dense row-major (Ns+1)x(Ns+1) per state: d_jac[(i*(Ns+1)+j)*ld + s]. */
+int pj_eval_jacobian_dense(const pj_mech* mech, int mode, int64_t n, const double* d_param,
+                           const double* d_phi, int64_t ld, double* d_jac, double* d_dphi,
+                           int* d_status, void* d_work, size_t work_bytes, void* stream);
+
+/* operation ids for pj_workspace_size */
+#define PJ_OP_SOURCE 0
+#define PJ_OP_JACOBIAN 1
+#define PJ_OP_NEWTON 2
+#define PJ_OP_VJP 3
+
+/* Device scratch (bytes) an operation needs for a batch of n states; 0 when
+ * the per-state working arrays fit in shared memory. */
+int pj_workspace_size(const pj_mech* mech, int op, int64_t n, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PYJAC_GB_H */

@@ -1,0 +1,91 @@
+"""ctypes loader for libpyjac_gb.so (the C ABI declared in include/pyjac_gb.h).
+
+Argument marshalling only.  Loading fails loudly when the library has not
+been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+PJ_OK, PJ_ERR_ARG, PJ_ERR_MECH, PJ_ERR_CUDA, PJ_ERR_NOMEM, PJ_ERR_UNSUPPORTED, PJ_ERR_TIMEOUT = range(7)
+PJ_CONP, PJ_CONV = 0, 1
+PJ_CSR, PJ_CSC, PJ_DENSE = 0, 1, 2
+PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP = 0, 1, 2, 3
+PJ_MAX_SP = 4
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_vp = C.c_void_p
+
+
+class pj_mech_desc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32),
+                ("W", _dp), ("T_mid", _dp), ("nasa_low", _dp), ("nasa_high", _dp),
+                ("kind", _ip), ("reversible", _ip), ("reac_sp", _ip), ("reac_nu", _ip),
+                ("prod_sp", _ip), ("prod_nu", _ip), ("A", _dp), ("beta", _dp), ("Ea", _dp),
+                ("A0", _dp), ("beta0", _dp), ("Ea0", _dp), ("troe", _dp), ("troe_n", _ip),
+                ("sri", _dp), ("eff_ptr", _ip), ("eff_sp", _ip), ("eff_val", _dp)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/pyjac_gb.h
+SIGNATURES = {
+    "pj_last_error": (C.c_char_p, []),
+    "pj_version": (C.c_char_p, []),
+    "pj_mech_create": (C.c_int, [C.POINTER(pj_mech_desc), C.POINTER(_vp)]),
+    "pj_mech_load": (C.c_int, [C.c_char_p, C.POINTER(_vp)]),
+    "pj_mech_free": (C.c_int, [_vp]),
+    "pj_mech_info": (C.c_int, [_vp, _ip, _ip, _ip]),
+    "pj_sparsity": (C.c_int, [_vp, C.c_int, _ip, _ip]),
+    "pj_eval_source_terms": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp,
+                                       _vp, C.c_size_t, _vp]),
+    "pj_eval_jacobian_sparse": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
+                                          _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pj_eval_jacobian_dense": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp,
+                                         _vp, C.c_size_t, _vp]),
+    "pj_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the shared library once; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"libpyjac_gb.so not built ({path}); run "
+                               "`python -m paper_1809_01029_gb300.build` (or __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        if not hasattr(lib, name):
+            continue
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PJError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().pj_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with code {code}: {msg}")
+        self.code = code
+
+
+def check(code, where):
+    if code != PJ_OK:
+        raise PJError(code, where)
+    return code

@@ -1,0 +1,195 @@
+"""Python binding of the C ABI (include/pyjac_gb.h).
+
+Functions named ``pj_*`` mirror the C entry points one to one (argument
+marshalling only: torch tensors are passed by device pointer, ``stream``
+defaults to torch's current stream).  The convenience wrappers below them
+allocate outputs with torch and call the same entry points.  Every step of
+the computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_MAX_SP, check)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+
+
+class Mechanism:
+    """Owner of a ``pj_mech*`` handle (freed on garbage collection)."""
+
+    def __init__(self, handle: C.c_void_p, name: str = ""):
+        self._h = handle
+        self.name = name
+        ns, nr, nnz = C.c_int32(), C.c_int32(), C.c_int32()
+        check(N.load().pj_mech_info(self._h, C.byref(ns), C.byref(nr), C.byref(nnz)), "pj_mech_info")
+        self.n_species, self.n_reactions, self.nnz = ns.value, nr.value, nnz.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sparsity(self, fmt=PJ_CSR):
+        ptr = np.zeros(self.n_species + 2, dtype=np.int32)
+        idx = np.zeros(max(self.nnz, 1), dtype=np.int32)
+        check(N.load().pj_sparsity(self._h, fmt, ptr.ctypes.data_as(N._ip), idx.ctypes.data_as(N._ip)),
+              "pj_sparsity")
+        return ptr, idx[: self.nnz]
+
+    def workspace_size(self, op, n):
+        b = C.c_size_t()
+        check(N.load().pj_workspace_size(self._h, op, n, C.byref(b)), "pj_workspace_size")
+        return b.value
+
+    def close(self):
+        if self._h is not None and N._lib is not None:
+            N._lib.pj_mech_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pj_mech_create(mech) -> Mechanism:
+    """Create a device mechanism from a description object with the fields of
+    ``pj_mech_desc`` (species data, reactions, efficiencies)."""
+    lib = N.load()
+    ns, nr = len(mech.W), len(mech.kind)
+    keep = dict(
+        W=_f64(mech.W), T_mid=_f64(mech.T_mid), nasa_low=_f64(mech.nasa_low).reshape(-1),
+        nasa_high=_f64(mech.nasa_high).reshape(-1), kind=_i32(mech.kind),
+        reversible=_i32(np.asarray(mech.reversible).astype(np.int32)),
+        reac_sp=_i32(mech.reac_sp).reshape(-1), reac_nu=_i32(mech.reac_nu).reshape(-1),
+        prod_sp=_i32(mech.prod_sp).reshape(-1), prod_nu=_i32(mech.prod_nu).reshape(-1),
+        A=_f64(mech.A), beta=_f64(mech.beta), Ea=_f64(mech.Ea), A0=_f64(mech.A0),
+        beta0=_f64(mech.beta0), Ea0=_f64(mech.Ea0), troe=_f64(mech.troe).reshape(-1),
+        troe_n=_i32(mech.troe_n), sri=_f64(mech.sri).reshape(-1), eff_ptr=_i32(mech.eff_ptr),
+        eff_sp=_i32(mech.eff_sp) if len(mech.eff_sp) else np.zeros(1, np.int32),
+        eff_val=_f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1))
+    d = N.pj_mech_desc()
+    d.n_species, d.n_reactions = ns, nr
+    for k, v in keep.items():
+        setattr(d, k, v.ctypes.data_as(N._ip if v.dtype == np.int32 else N._dp))
+    h = C.c_void_p()
+    check(lib.pj_mech_create(C.byref(d), C.byref(h)), "pj_mech_create")
+    return Mechanism(h, getattr(mech, "name", ""))
+
+
+def pj_mech_load(path: str) -> Mechanism:
+    h = C.c_void_p()
+    check(N.load().pj_mech_load(path.encode(), C.byref(h)), "pj_mech_load")
+    return Mechanism(h, path)
+
+
+def pj_sparsity(mech: Mechanism, fmt=PJ_CSR):
+    return mech.sparsity(fmt)
+
+
+def pj_workspace_size(mech: Mechanism, op, n):
+    return mech.workspace_size(op, n)
+
+
+def pj_eval_source_terms(mech, mode, n, param, phi, ld, dphi, status=None, work=None, work_bytes=0,
+                         stream=None):
+    return check(N.load().pj_eval_source_terms(mech.handle, mode, n, _ptr(param), _ptr(phi), ld, _ptr(dphi),
+                                                _ptr(status), _ptr(work), work_bytes, _stream(stream)),
+                 "pj_eval_source_terms")
+
+
+def pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, vals, dphi=None, status=None, work=None,
+                            work_bytes=0, stream=None):
+    return check(N.load().pj_eval_jacobian_sparse(mech.handle, mode, fmt, n, _ptr(param), _ptr(phi), ld,
+                                                   _ptr(vals), _ptr(dphi), _ptr(status), _ptr(work),
+                                                   work_bytes, _stream(stream)),
+                 "pj_eval_jacobian_sparse")
+
+
+def pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, jac, dphi=None, status=None, work=None,
+                           work_bytes=0, stream=None):
+    return check(N.load().pj_eval_jacobian_dense(mech.handle, mode, n, _ptr(param), _ptr(phi), ld, _ptr(jac),
+                                                  _ptr(dphi), _ptr(status), _ptr(work), work_bytes,
+                                                  _stream(stream)),
+                 "pj_eval_jacobian_dense")
+
+
+# ---------------------------------------------------------------------------
+# convenience wrappers (torch tensors in, torch tensors out)
+# ---------------------------------------------------------------------------
+def _check_batch(mech, phi, param):
+    import torch
+    if phi.dtype != torch.float64 or param.dtype != torch.float64:
+        raise TypeError("phi and param must be float64")
+    if not (phi.is_cuda and param.is_cuda):
+        raise TypeError("phi and param must be CUDA tensors")
+    if phi.dim() != 2 or phi.shape[0] != mech.n_species + 1 or phi.stride(1) != 1:
+        raise ValueError("phi must be [Ns+1, n] with unit stride along states")
+    if param.dim() != 1 or param.shape[0] != phi.shape[1] or param.stride(0) != 1:
+        raise ValueError("param must be [n] contiguous")
+    return phi.shape[1], max(phi.stride(0), 1)
+
+
+def _workspace(mech, op, n, device):
+    import torch
+    b = mech.workspace_size(op, n)
+    return (torch.empty(b, dtype=torch.uint8, device=device), b) if b else (None, 0)
+
+
+def source_terms(mech, mode, phi, param, out=None, status=None, stream=None):
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    if out is None:
+        out = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    work, wb = _workspace(mech, PJ_OP_SOURCE, n, phi.device)
+    pj_eval_source_terms(mech, mode, n, param, phi, ld, out, status, work, wb, stream)
+    return out
+
+
+def jacobian_sparse(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=None, stream=None):
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    if out is None:
+        out = torch.empty((mech.nnz, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
+    pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, out, dphi, status, work, wb, stream)
+    return out
+
+
+def jacobian_dense(mech, mode, phi, param, out=None, dphi=None, status=None, stream=None):
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    N1 = mech.n_species + 1
+    if out is None:
+        out = torch.empty((N1 * N1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
+    pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, out, dphi, status, work, wb, stream)
+    return out

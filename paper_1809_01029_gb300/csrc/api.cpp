@@ -1,0 +1,79 @@
+// C-ABI evaluation entry points: argument validation and dispatch to the
+// kernels in kinetics.cu.  No host synchronisation, no allocation.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "pj_internal.h"
+
+namespace pj {
+int launch_source(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
+                  double* out, int* status, void* work, size_t work_bytes, cudaStream_t st);
+int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
+                    int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
+                    cudaStream_t st);
+size_t workspace_bytes(int arrays, int ns, int64_t n);
+int source_arrays();
+int jacobian_arrays();
+
+int check_common(const char* fn, const pj_mech* m, int mode, int64_t n, int64_t ld, const void* param,
+                 const void* phi, const void* out) {
+  const std::string f(fn);
+  if (!m) return fail(PJ_ERR_ARG, f + ": null mechanism");
+  if (mode != PJ_CONP && mode != PJ_CONV) return fail(PJ_ERR_ARG, f + ": mode must be PJ_CONP or PJ_CONV");
+  if (n < 0) return fail(PJ_ERR_ARG, f + ": n < 0");
+  if (ld < n || ld < 1) return fail(PJ_ERR_ARG, f + ": ld must be >= max(n, 1)");
+  if (n > 0 && (!param || !phi || !out)) return fail(PJ_ERR_ARG, f + ": null buffer");
+  if (m->device < 0) return fail(PJ_ERR_CUDA, f + ": mechanism has no device copy (no CUDA device at creation)");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return check_cuda(e, "cudaGetDevice");
+  if (dev != m->device)
+    return fail(PJ_ERR_ARG, f + ": current device " + std::to_string(dev) + " differs from the mechanism's device " +
+                                std::to_string(m->device));
+  return PJ_OK;
+}
+}  // namespace pj
+
+using namespace pj;
+
+extern "C" int pj_workspace_size(const pj_mech* m, int op, int64_t n, size_t* bytes) {
+  if (!m || !bytes) return fail(PJ_ERR_ARG, "pj_workspace_size: null argument");
+  if (n < 0) return fail(PJ_ERR_ARG, "pj_workspace_size: n < 0");
+  switch (op) {
+    case PJ_OP_SOURCE: *bytes = workspace_bytes(source_arrays(), m->ns, n); return PJ_OK;
+    case PJ_OP_JACOBIAN:
+    case PJ_OP_NEWTON: *bytes = workspace_bytes(jacobian_arrays(), m->ns, n); return PJ_OK;
+    default: return fail(PJ_ERR_ARG, "pj_workspace_size: unknown op");
+  }
+}
+
+extern "C" int pj_eval_source_terms(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi,
+                                    int64_t ld, double* dphi, int* status, void* work, size_t work_bytes,
+                                    void* stream) {
+  int rc = check_common("pj_eval_source_terms", m, mode, n, ld, param, phi, dphi);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_source(m->dm, mode, n, param, phi, ld, dphi, status, work, work_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int pj_eval_jacobian_sparse(const pj_mech* m, int mode, int fmt, int64_t n, const double* param,
+                                       const double* phi, int64_t ld, double* vals, double* dphi, int* status,
+                                       void* work, size_t work_bytes, void* stream) {
+  if (fmt != PJ_CSR && fmt != PJ_CSC) return fail(PJ_ERR_ARG, "pj_eval_jacobian_sparse: fmt must be PJ_CSR or PJ_CSC");
+  int rc = check_common("pj_eval_jacobian_sparse", m, mode, n, ld, param, phi, vals);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_jacobian(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, work, work_bytes,
+                         (cudaStream_t)stream);
+}
+
+extern "C" int pj_eval_jacobian_dense(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi,
+                                      int64_t ld, double* jac, double* dphi, int* status, void* work,
+                                      size_t work_bytes, void* stream) {
+  int rc = check_common("pj_eval_jacobian_dense", m, mode, n, ld, param, phi, jac);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_jacobian(m->dm, mode, PJ_DENSE, n, param, phi, ld, jac, dphi, status, work, work_bytes,
+                         (cudaStream_t)stream);
+}

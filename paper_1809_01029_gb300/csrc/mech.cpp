@@ -1,0 +1,486 @@
+// Host side of libpyjac_gb: mechanism validation, packing of the kernel
+// constants, the fixed sparsity pattern of the exact Jacobian (Sec. 3.3) and
+// the static full-index -> sparse-index maps the paper proposes in place of a
+// per-entry search of the compressed row (Sec. 3.3, last paragraph).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+
+#include "pj_internal.h"
+
+namespace pj {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int check_cuda(int err, const char* what) {
+  if (err == cudaSuccess) return PJ_OK;
+  return fail(err == cudaErrorMemoryAllocation ? PJ_ERR_NOMEM : PJ_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString((cudaError_t)err));
+}
+
+// Net stoichiometric coefficient of every species in reaction i.
+static std::vector<int> net_nu(const pj_mech* m, int i) {
+  std::vector<int> nu(m->ns, 0);
+  for (int a = 0; a < PJ_MAX_SP; a++) {
+    int k = m->reac_sp[i * PJ_MAX_SP + a];
+    if (k >= 0) nu[k] -= m->reac_nu[i * PJ_MAX_SP + a];
+    k = m->prod_sp[i * PJ_MAX_SP + a];
+    if (k >= 0) nu[k] += m->prod_nu[i * PJ_MAX_SP + a];
+  }
+  return nu;
+}
+
+static std::vector<double> alpha_of(const pj_mech* m, int i) {
+  std::vector<double> a(m->ns, 1.0);
+  for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++) a[m->eff_sp[e]] = m->eff_val[e];
+  return a;
+}
+
+// Species (< Ns-1) on which reaction i's rate depends, and whether that is
+// every species (bath gas in the rate, or a non-unit bath-gas efficiency).
+static bool rate_dependence(const pj_mech* m, int i, std::vector<char>& dep) {
+  const int ns = m->ns, bath = ns - 1;
+  dep.assign(ns - 1, 0);
+  bool dense = false;
+  auto member = [&](int k) {
+    if (k == bath) dense = true;
+    else if (k >= 0) dep[k] = 1;
+  };
+  for (int a = 0; a < PJ_MAX_SP; a++) member(m->reac_sp[i * PJ_MAX_SP + a]);
+  if (m->rev[i])
+    for (int a = 0; a < PJ_MAX_SP; a++) member(m->prod_sp[i * PJ_MAX_SP + a]);
+  if (m->kind[i] != PJ_ELEMENTARY) {
+    std::vector<double> al = alpha_of(m, i);
+    for (int k = 0; k < ns - 1; k++)
+      if (al[k] != al[bath]) dep[k] = 1;
+    if (al[bath] != 1.0) dense = true;
+  }
+  if (dense) std::fill(dep.begin(), dep.end(), 1);
+  return dense;
+}
+
+static int validate(const pj_mech* m) {
+  const int ns = m->ns, nr = m->nr;
+  if (ns < 2) return fail(PJ_ERR_MECH, "need at least 2 species");
+  if (nr < 0) return fail(PJ_ERR_MECH, "negative reaction count");
+  for (int k = 0; k < ns; k++) {
+    if (!(m->W[k] > 0) || !std::isfinite(m->W[k])) return fail(PJ_ERR_MECH, "species " + std::to_string(k) + ": W must be > 0");
+    if (!std::isfinite(m->T_mid[k])) return fail(PJ_ERR_MECH, "species " + std::to_string(k) + ": bad T_mid");
+    for (int j = 0; j < 7; j++)
+      if (!std::isfinite(m->nasa_low[k * 7 + j]) || !std::isfinite(m->nasa_high[k * 7 + j]))
+        return fail(PJ_ERR_MECH, "species " + std::to_string(k) + ": non-finite NASA coefficient");
+  }
+  if (m->eff_ptr.size() != (size_t)nr + 1 || m->eff_ptr[0] != 0)
+    return fail(PJ_ERR_MECH, "eff_ptr must have Nr+1 entries starting at 0");
+  for (int i = 0; i < nr; i++) {
+    std::string tag = "reaction " + std::to_string(i) + ": ";
+    if (m->kind[i] < PJ_ELEMENTARY || m->kind[i] > PJ_SRI) return fail(PJ_ERR_MECH, tag + "bad kind");
+    int nre = 0, npr = 0;
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      for (int side = 0; side < 2; side++) {
+        int k = side ? m->prod_sp[i * PJ_MAX_SP + a] : m->reac_sp[i * PJ_MAX_SP + a];
+        int v = side ? m->prod_nu[i * PJ_MAX_SP + a] : m->reac_nu[i * PJ_MAX_SP + a];
+        if (k < -1 || k >= ns) return fail(PJ_ERR_MECH, tag + "species index out of range");
+        if (k >= 0) {
+          if (v < 1 || v > 8) return fail(PJ_ERR_MECH, tag + "stoichiometric coefficient must be 1..8");
+          (side ? npr : nre)++;
+        }
+      }
+    }
+    if (nre == 0 || npr == 0) return fail(PJ_ERR_MECH, tag + "needs at least one reactant and one product");
+    if (!(m->A[i] > 0) || !std::isfinite(m->A[i])) return fail(PJ_ERR_MECH, tag + "A must be > 0");
+    if (!std::isfinite(m->beta[i]) || !std::isfinite(m->Ea[i])) return fail(PJ_ERR_MECH, tag + "bad beta/Ea");
+    if (m->kind[i] >= PJ_LINDEMANN) {
+      if (!(m->A0[i] > 0) || !std::isfinite(m->A0[i])) return fail(PJ_ERR_MECH, tag + "A0 must be > 0");
+      if (!std::isfinite(m->beta0[i]) || !std::isfinite(m->Ea0[i])) return fail(PJ_ERR_MECH, tag + "bad beta0/Ea0");
+    }
+    if (m->kind[i] == PJ_TROE) {
+      int tn = m->troe_n[i];
+      const double* t = &m->troe[i * 4];
+      if (tn != 3 && tn != 4) return fail(PJ_ERR_MECH, tag + "Troe needs 3 or 4 parameters");
+      if (t[1] == 0 || t[2] == 0 || !std::isfinite(t[0])) return fail(PJ_ERR_MECH, tag + "Troe T3/T1 must be nonzero");
+    }
+    if (m->kind[i] == PJ_SRI) {
+      const double* s = &m->sri[i * 5];
+      if (s[2] == 0 || !(s[3] > 0)) return fail(PJ_ERR_MECH, tag + "SRI needs c != 0 and d > 0");
+    }
+    if (m->eff_ptr[i + 1] < m->eff_ptr[i]) return fail(PJ_ERR_MECH, tag + "eff_ptr not monotone");
+    for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++) {
+      if (m->eff_sp[e] < 0 || m->eff_sp[e] >= ns) return fail(PJ_ERR_MECH, tag + "efficiency species out of range");
+      if (!std::isfinite(m->eff_val[e]) || m->eff_val[e] < 0) return fail(PJ_ERR_MECH, tag + "bad efficiency");
+    }
+  }
+  return PJ_OK;
+}
+
+static void build_pattern(pj_mech* m) {
+  const int ns = m->ns, N = ns + 1;
+  std::vector<char> mask((size_t)N * N, 0);
+  for (int j = 0; j < N; j++) {
+    mask[0 * N + j] = mask[1 * N + j] = 1;
+    mask[(size_t)j * N + 0] = mask[(size_t)j * N + 1] = 1;
+    mask[(size_t)j * N + j] = 1;
+  }
+  std::vector<char> dep;
+  for (int i = 0; i < m->nr; i++) {
+    rate_dependence(m, i, dep);
+    std::vector<int> nu = net_nu(m, i);
+    for (int k = 0; k < ns - 1; k++) {
+      if (nu[k] == 0) continue;
+      for (int j = 0; j < ns - 1; j++)
+        if (dep[j]) mask[(size_t)(k + 2) * N + (j + 2)] = 1;
+    }
+  }
+  m->csr_ptr.assign(N + 1, 0);
+  m->csr_idx.clear();
+  m->pos_csr.assign((size_t)N * N, -1);
+  for (int i = 0; i < N; i++) {
+    for (int j = 0; j < N; j++)
+      if (mask[(size_t)i * N + j]) {
+        m->pos_csr[(size_t)i * N + j] = (int32_t)m->csr_idx.size();
+        m->csr_idx.push_back(j);
+      }
+    m->csr_ptr[i + 1] = (int32_t)m->csr_idx.size();
+  }
+  m->csc_ptr.assign(N + 1, 0);
+  m->csc_idx.clear();
+  m->pos_csc.assign((size_t)N * N, -1);
+  for (int j = 0; j < N; j++) {
+    for (int i = 0; i < N; i++)
+      if (mask[(size_t)i * N + j]) {
+        m->pos_csc[(size_t)i * N + j] = (int32_t)m->csc_idx.size();
+        m->csc_idx.push_back(i);
+      }
+    m->csc_ptr[j + 1] = (int32_t)m->csc_idx.size();
+  }
+  m->nnz = (int32_t)m->csr_idx.size();
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int mech_build(pj_mech* m) {
+  int rc = validate(m);
+  if (rc) return rc;
+  build_pattern(m);
+  const int ns = m->ns, nr = m->nr, N = ns + 1, bath = ns - 1;
+
+  // kernel order: stable sort by kind so that each kind's code runs as a block
+  m->perm.resize(nr);
+  for (int i = 0; i < nr; i++) m->perm[i] = i;
+  std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) { return m->kind[a] < m->kind[b]; });
+
+  std::vector<double> nasa((size_t)ns * NASA_STRIDE, 0.0), wfac(ns);
+  for (int k = 0; k < ns; k++) {
+    for (int r = 0; r < 2; r++) {
+      const double* a = r == 0 ? &m->nasa_low[k * 7] : &m->nasa_high[k * 7];
+      double* b = &nasa[(size_t)k * NASA_STRIDE + r * 16];
+      for (int j = 0; j < 7; j++) b[j] = a[j];
+      b[7] = a[1] / 2; b[8] = a[2] / 3; b[9] = a[3] / 4; b[10] = a[4] / 5;
+      b[11] = a[2] / 2; b[12] = a[3] / 3; b[13] = a[4] / 4;
+      b[14] = m->T_mid[k];
+    }
+    wfac[k] = 1.0 - m->W[k] / m->W[bath];
+  }
+
+  std::vector<Rxn> rx(nr);
+  std::vector<int32_t> eff_sp;
+  std::vector<double> eff_am1;
+  std::vector<RowNu> rows;
+  std::vector<char> dep;
+  for (int q = 0; q < nr; q++) {
+    const int i = m->perm[q];
+    Rxn& r = rx[q];
+    std::memset(&r, 0, sizeof(Rxn));
+    r.kind = m->kind[i];
+    r.rev = m->rev[i] ? 1 : 0;
+    r.lnA = std::log(m->A[i]);
+    r.beta = m->beta[i];
+    r.theta = m->Ea[i] / R_CAL;
+    if (r.kind >= PJ_LINDEMANN) {
+      r.lnA0 = std::log(m->A0[i]);
+      r.beta0 = m->beta0[i];
+      r.theta0 = m->Ea0[i] / R_CAL;
+    }
+    if (r.kind == PJ_TROE) {
+      const double* t = &m->troe[i * 4];
+      r.fp[0] = t[0]; r.fp[1] = 1.0 / t[1]; r.fp[2] = 1.0 / t[2];
+      r.fp[3] = m->troe_n[i] == 4 ? t[3] : 0.0;
+      r.fp[4] = m->troe_n[i] == 4 ? 1.0 : 0.0;
+    } else if (r.kind == PJ_SRI) {
+      const double* s = &m->sri[i * 5];
+      r.fp[0] = s[0]; r.fp[1] = s[1]; r.fp[2] = 1.0 / s[2]; r.fp[3] = s[3]; r.fp[4] = s[4];
+    }
+    for (int a = 0; a < 2 * PJ_MAX_SP; a++) r.sp[a] = -1;
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (m->reac_sp[i * PJ_MAX_SP + a] >= 0) {
+        r.sp[r.nreac] = m->reac_sp[i * PJ_MAX_SP + a];
+        r.nu[r.nreac] = m->reac_nu[i * PJ_MAX_SP + a];
+        r.nreac++;
+      }
+      if (m->prod_sp[i * PJ_MAX_SP + a] >= 0) {
+        r.sp[PJ_MAX_SP + r.nprod] = m->prod_sp[i * PJ_MAX_SP + a];
+        r.nu[PJ_MAX_SP + r.nprod] = m->prod_nu[i * PJ_MAX_SP + a];
+        r.nprod++;
+      }
+    }
+    std::vector<int> nu = net_nu(m, i);
+    double dnu = 0, dW = 0;
+    for (int k = 0; k < ns; k++) {
+      dnu += nu[k];
+      if (k < bath) dW += nu[k] * wfac[k];
+    }
+    r.dnu = dnu;
+    r.dW = dW;
+    std::vector<double> al = alpha_of(m, i);
+    r.alpha_bath = r.kind != PJ_ELEMENTARY ? al[bath] : 1.0;
+    r.eff_lo = (int32_t)eff_sp.size();
+    if (r.kind != PJ_ELEMENTARY) {
+      for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++) {
+        if (m->eff_val[e] == 1.0) continue;  // default efficiency: no term
+        eff_sp.push_back(m->eff_sp[e]);
+        eff_am1.push_back(m->eff_val[e] - 1.0);
+      }
+    }
+    r.eff_hi = (int32_t)eff_sp.size();
+    r.row_lo = (int32_t)rows.size();
+    for (int k = 0; k < bath; k++)
+      if (nu[k] != 0) rows.push_back(RowNu{k, nu[k]});
+    r.row_hi = (int32_t)rows.size();
+    r.dense = rate_dependence(m, i, dep) ? 1 : 0;
+  }
+
+  // one device allocation holding every constant array
+  const size_t o_nasa = 0;
+  const size_t o_wfac = align256(o_nasa + nasa.size() * sizeof(double));
+  const size_t o_rxn = align256(o_wfac + wfac.size() * sizeof(double));
+  const size_t o_esp = align256(o_rxn + rx.size() * sizeof(Rxn));
+  const size_t o_eam = align256(o_esp + eff_sp.size() * sizeof(int32_t));
+  const size_t o_rows = align256(o_eam + eff_am1.size() * sizeof(double));
+  const size_t o_pcsr = align256(o_rows + rows.size() * sizeof(RowNu));
+  const size_t o_pcsc = align256(o_pcsr + (size_t)N * N * sizeof(int32_t));
+  const size_t total = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
+
+  std::vector<char> blob(total, 0);
+  auto put = [&](size_t off, const void* src, size_t bytes) { if (bytes) std::memcpy(blob.data() + off, src, bytes); };
+  put(o_nasa, nasa.data(), nasa.size() * sizeof(double));
+  put(o_wfac, wfac.data(), wfac.size() * sizeof(double));
+  put(o_rxn, rx.data(), rx.size() * sizeof(Rxn));
+  put(o_esp, eff_sp.data(), eff_sp.size() * sizeof(int32_t));
+  put(o_eam, eff_am1.data(), eff_am1.size() * sizeof(double));
+  put(o_rows, rows.data(), rows.size() * sizeof(RowNu));
+  put(o_pcsr, m->pos_csr.data(), m->pos_csr.size() * sizeof(int32_t));
+  put(o_pcsc, m->pos_csc.data(), m->pos_csc.size() * sizeof(int32_t));
+
+  // Without any CUDA device the handle stays host-only: its pattern can be
+  // queried, evaluation calls fail with PJ_ERR_CUDA.
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    m->device = -1;
+    return PJ_OK;
+  }
+  int dev = 0;
+  if ((rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+  void* d = nullptr;
+  if ((rc = check_cuda(cudaMalloc(&d, total), "cudaMalloc(mechanism constants)"))) return rc;
+  if ((rc = check_cuda(cudaMemcpy(d, blob.data(), total, cudaMemcpyHostToDevice), "cudaMemcpy(mechanism constants)"))) {
+    cudaFree(d);
+    return rc;
+  }
+  m->device = dev;
+  m->dev_blob = d;
+  m->dev_bytes = total;
+  char* b = static_cast<char*>(d);
+  DevMech& dm = m->dm;
+  dm.ns = ns;
+  dm.nr = nr;
+  dm.N = N;
+  dm.nnz = m->nnz;
+  dm.log_pstd_over_r = std::log(P_STD / RU);
+  dm.nasa = reinterpret_cast<const double*>(b + o_nasa);
+  dm.wfac = reinterpret_cast<const double*>(b + o_wfac);
+  dm.rxn = reinterpret_cast<const Rxn*>(b + o_rxn);
+  dm.eff_sp = reinterpret_cast<const int32_t*>(b + o_esp);
+  dm.eff_am1 = reinterpret_cast<const double*>(b + o_eam);
+  dm.rows = reinterpret_cast<const RowNu*>(b + o_rows);
+  dm.pos_csr = reinterpret_cast<const int32_t*>(b + o_pcsr);
+  dm.pos_csc = reinterpret_cast<const int32_t*>(b + o_pcsc);
+  return PJ_OK;
+}
+
+void mech_release(pj_mech* m) {
+  if (m && m->dev_blob) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != m->device) cudaSetDevice(m->device);
+    cudaFree(m->dev_blob);
+    if (cur != m->device && cur >= 0) cudaSetDevice(cur);
+    m->dev_blob = nullptr;
+  }
+}
+
+}  // namespace pj
+
+using namespace pj;
+
+extern "C" const char* pj_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* pj_version(void) { return "pyjac_gb 0.1 (sm_103a)"; }
+
+extern "C" int pj_mech_create(const pj_mech_desc* d, pj_mech** out) {
+  if (!d || !out) return fail(PJ_ERR_ARG, "pj_mech_create: null argument");
+  *out = nullptr;
+  const int ns = d->n_species, nr = d->n_reactions;
+  if (ns < 2 || nr < 0) return fail(PJ_ERR_MECH, "pj_mech_create: bad sizes");
+  if (!d->W || !d->T_mid || !d->nasa_low || !d->nasa_high || !d->eff_ptr ||
+      (nr > 0 && (!d->kind || !d->reversible || !d->reac_sp || !d->reac_nu || !d->prod_sp ||
+                  !d->prod_nu || !d->A || !d->beta || !d->Ea || !d->A0 || !d->beta0 ||
+                  !d->Ea0 || !d->troe || !d->troe_n || !d->sri)))
+    return fail(PJ_ERR_ARG, "pj_mech_create: null array in description");
+  pj_mech* m = new (std::nothrow) pj_mech();
+  if (!m) return fail(PJ_ERR_NOMEM, "pj_mech_create: out of host memory");
+  try {
+    m->ns = ns;
+    m->nr = nr;
+    m->W.assign(d->W, d->W + ns);
+    m->T_mid.assign(d->T_mid, d->T_mid + ns);
+    m->nasa_low.assign(d->nasa_low, d->nasa_low + 7 * ns);
+    m->nasa_high.assign(d->nasa_high, d->nasa_high + 7 * ns);
+    auto cp_i = [&](std::vector<int32_t>& v, const int32_t* s, size_t len) { v.assign(s, s + len); };
+    auto cp_d = [&](std::vector<double>& v, const double* s, size_t len) { v.assign(s, s + len); };
+    if (nr > 0) {
+      cp_i(m->kind, d->kind, nr);
+      cp_i(m->rev, d->reversible, nr);
+      cp_i(m->reac_sp, d->reac_sp, (size_t)nr * PJ_MAX_SP);
+      cp_i(m->reac_nu, d->reac_nu, (size_t)nr * PJ_MAX_SP);
+      cp_i(m->prod_sp, d->prod_sp, (size_t)nr * PJ_MAX_SP);
+      cp_i(m->prod_nu, d->prod_nu, (size_t)nr * PJ_MAX_SP);
+      cp_d(m->A, d->A, nr);
+      cp_d(m->beta, d->beta, nr);
+      cp_d(m->Ea, d->Ea, nr);
+      cp_d(m->A0, d->A0, nr);
+      cp_d(m->beta0, d->beta0, nr);
+      cp_d(m->Ea0, d->Ea0, nr);
+      cp_d(m->troe, d->troe, (size_t)nr * 4);
+      cp_i(m->troe_n, d->troe_n, nr);
+      cp_d(m->sri, d->sri, (size_t)nr * 5);
+    }
+    cp_i(m->eff_ptr, d->eff_ptr, (size_t)nr + 1);
+    const int ne = m->eff_ptr[nr];
+    if (ne < 0) { delete m; return fail(PJ_ERR_MECH, "pj_mech_create: negative efficiency count"); }
+    if (ne > 0 && (!d->eff_sp || !d->eff_val)) { delete m; return fail(PJ_ERR_ARG, "pj_mech_create: null efficiency arrays"); }
+    if (ne > 0) {
+      cp_i(m->eff_sp, d->eff_sp, ne);
+      cp_d(m->eff_val, d->eff_val, ne);
+    }
+  } catch (...) {
+    delete m;
+    return fail(PJ_ERR_NOMEM, "pj_mech_create: out of host memory");
+  }
+  int rc = mech_build(m);
+  if (rc) {
+    mech_release(m);
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return PJ_OK;
+}
+
+extern "C" int pj_mech_free(pj_mech* m) {
+  if (!m) return PJ_OK;
+  mech_release(m);
+  delete m;
+  return PJ_OK;
+}
+
+extern "C" int pj_mech_info(const pj_mech* m, int32_t* ns, int32_t* nr, int32_t* nnz) {
+  if (!m) return fail(PJ_ERR_ARG, "pj_mech_info: null mechanism");
+  if (ns) *ns = m->ns;
+  if (nr) *nr = m->nr;
+  if (nnz) *nnz = m->nnz;
+  return PJ_OK;
+}
+
+extern "C" int pj_sparsity(const pj_mech* m, int fmt, int32_t* ptr, int32_t* idx) {
+  if (!m || !ptr || !idx) return fail(PJ_ERR_ARG, "pj_sparsity: null argument");
+  if (fmt != PJ_CSR && fmt != PJ_CSC) return fail(PJ_ERR_ARG, "pj_sparsity: fmt must be PJ_CSR or PJ_CSC");
+  const auto& p = fmt == PJ_CSR ? m->csr_ptr : m->csc_ptr;
+  const auto& x = fmt == PJ_CSR ? m->csr_idx : m->csc_idx;
+  std::memcpy(ptr, p.data(), p.size() * sizeof(int32_t));
+  std::memcpy(idx, x.data(), x.size() * sizeof(int32_t));
+  return PJ_OK;
+}
+
+// ---- PJMECH text file ------------------------------------------------------
+extern "C" int pj_mech_load(const char* path, pj_mech** out) {
+  if (!path || !out) return fail(PJ_ERR_ARG, "pj_mech_load: null argument");
+  std::ifstream in(path);
+  if (!in) return fail(PJ_ERR_ARG, std::string("pj_mech_load: cannot open ") + path);
+  std::string tok;
+  auto expect = [&](const char* w) { return (in >> tok) && tok == w; };
+  if (!expect("PJMECH") || !expect("1")) return fail(PJ_ERR_MECH, "pj_mech_load: not a PJMECH 1 file");
+  int ns = 0, nr = 0;
+  if (!expect("SPECIES") || !(in >> ns) || ns < 2 || ns > 1000000) return fail(PJ_ERR_MECH, "pj_mech_load: bad SPECIES record");
+  std::vector<double> W(ns), Tm(ns), lo(7 * ns), hi(7 * ns);
+  for (int k = 0; k < ns; k++) {
+    std::string name;
+    int comp;
+    if (!(in >> name >> W[k] >> Tm[k])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated species record");
+    for (int e = 0; e < 5; e++)
+      if (!(in >> comp)) return fail(PJ_ERR_MECH, "pj_mech_load: truncated species composition");
+    for (int j = 0; j < 7; j++) if (!(in >> lo[k * 7 + j])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated NASA data");
+    for (int j = 0; j < 7; j++) if (!(in >> hi[k * 7 + j])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated NASA data");
+  }
+  if (!expect("REACTIONS") || !(in >> nr) || nr < 0 || nr > 10000000) return fail(PJ_ERR_MECH, "pj_mech_load: bad REACTIONS record");
+  std::vector<int32_t> kind(nr), rev(nr), rsp((size_t)nr * PJ_MAX_SP, -1), rnu((size_t)nr * PJ_MAX_SP, 0),
+      psp((size_t)nr * PJ_MAX_SP, -1), pnu((size_t)nr * PJ_MAX_SP, 0), tn(nr), eptr(nr + 1, 0), esp;
+  std::vector<double> A(nr), b(nr), Ea(nr), A0(nr), b0(nr), Ea0(nr), troe((size_t)nr * 4), sri((size_t)nr * 5), eval;
+  for (int i = 0; i < nr; i++) {
+    int cnt;
+    if (!(in >> kind[i] >> rev[i])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated reaction record");
+    for (int side = 0; side < 2; side++) {
+      if (!(in >> cnt) || cnt < 0 || cnt > PJ_MAX_SP) return fail(PJ_ERR_MECH, "pj_mech_load: bad participant count");
+      for (int a = 0; a < cnt; a++) {
+        int32_t* sp = side ? &psp[(size_t)i * PJ_MAX_SP] : &rsp[(size_t)i * PJ_MAX_SP];
+        int32_t* nu = side ? &pnu[(size_t)i * PJ_MAX_SP] : &rnu[(size_t)i * PJ_MAX_SP];
+        if (!(in >> sp[a] >> nu[a])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated participants");
+      }
+    }
+    if (!(in >> A[i] >> b[i] >> Ea[i] >> A0[i] >> b0[i] >> Ea0[i] >> tn[i])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated rate data");
+    for (int j = 0; j < 4; j++) if (!(in >> troe[(size_t)i * 4 + j])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated Troe data");
+    for (int j = 0; j < 5; j++) if (!(in >> sri[(size_t)i * 5 + j])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated SRI data");
+    int ne;
+    if (!(in >> ne) || ne < 0 || ne > 1000000) return fail(PJ_ERR_MECH, "pj_mech_load: bad efficiency count");
+    for (int e = 0; e < ne; e++) {
+      int32_t k;
+      double v;
+      if (!(in >> k >> v)) return fail(PJ_ERR_MECH, "pj_mech_load: truncated efficiencies");
+      esp.push_back(k);
+      eval.push_back(v);
+    }
+    eptr[i + 1] = (int32_t)esp.size();
+  }
+  if (!expect("END")) return fail(PJ_ERR_MECH, "pj_mech_load: missing END");
+  pj_mech_desc d{};
+  d.n_species = ns;
+  d.n_reactions = nr;
+  d.W = W.data(); d.T_mid = Tm.data(); d.nasa_low = lo.data(); d.nasa_high = hi.data();
+  d.kind = kind.data(); d.reversible = rev.data();
+  d.reac_sp = rsp.data(); d.reac_nu = rnu.data(); d.prod_sp = psp.data(); d.prod_nu = pnu.data();
+  d.A = A.data(); d.beta = b.data(); d.Ea = Ea.data(); d.A0 = A0.data(); d.beta0 = b0.data(); d.Ea0 = Ea0.data();
+  d.troe = troe.data(); d.troe_n = tn.data(); d.sri = sri.data();
+  d.eff_ptr = eptr.data(); d.eff_sp = esp.data(); d.eff_val = eval.data();
+  return pj_mech_create(&d, out);
+}

@@ -1,0 +1,87 @@
+// Internal definitions shared by the host-side mechanism code and the CUDA
+// kernels of libpyjac_gb: packed mechanism constants and launch helpers.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pyjac_gb.h"
+
+namespace pj {
+
+// physical constants, SI with kmol
+constexpr double RU = 8314.46261815324;      // J / (kmol K)
+constexpr double R_CAL = 1.98720425864083;   // cal / (mol K)
+constexpr double P_STD = 101325.0;           // Pa
+constexpr double LN10 = 2.302585092994045684;
+
+// per-species NASA-7 block: two ranges of 16 doubles
+//   [0..6]  a0..a6
+//   [7..10] a1/2, a2/3, a3/4, a4/5   (enthalpy polynomial)
+//   [11..13] a2/2, a3/3, a4/4        (entropy polynomial)
+//   [14]    T_mid (same in both ranges), [15] unused
+constexpr int NASA_STRIDE = 32;
+
+// One reaction, packed for warp-uniform loads (every thread of a warp reads
+// the same record).  Reactions are stored in kernel order (see perm).
+struct alignas(16) Rxn {
+  double lnA, beta, theta;        // k = exp(lnA + beta lnT - theta/T), theta = Ea/R_cal [K]
+  double lnA0, beta0, theta0;     // low-pressure limit (falloff)
+  double dnu;                     // sum_k nu_k (equilibrium-constant pressure factor)
+  double dW;                      // sum_{k<Ns-1} nu_k (1 - W_k/W_Ns)
+  double alpha_bath;              // third-body efficiency of the bath gas
+  double fp[5];                   // Troe: a, 1/T3, 1/T1, T2, has_T2 ; SRI: a, b, 1/c, d, e
+  int32_t kind, rev;
+  int32_t nreac, nprod;
+  int32_t sp[2 * PJ_MAX_SP];      // reactants [0, nreac), products [PJ_MAX_SP, PJ_MAX_SP + nprod)
+  int32_t nu[2 * PJ_MAX_SP];
+  int32_t eff_lo, eff_hi;         // non-default efficiencies in eff_sp / eff_am1
+  int32_t row_lo, row_hi;         // species rows (k < Ns-1, net nu != 0) in rows[]
+  int32_t dense;                  // rate depends on every species (bath gas involved)
+  int32_t pad;
+};
+
+struct RowNu {
+  int32_t k;      // species index (< Ns-1)
+  int32_t nu;     // net stoichiometric coefficient
+};
+
+// Kernel view of a mechanism (POD, passed by value).
+struct DevMech {
+  int32_t ns, nr, N, nnz;
+  double log_pstd_over_r;         // ln(P_std / R)
+  const double* nasa;             // [ns * NASA_STRIDE]
+  const double* wfac;             // [ns] 1 - W_k / W_{Ns-1}
+  const Rxn* rxn;                 // [nr]
+  const int32_t* eff_sp;          // [n_eff]
+  const double* eff_am1;          // [n_eff] alpha - 1
+  const RowNu* rows;              // [n_rows]
+  const int32_t* pos_csr;         // [N*N] full -> CSR value index, -1 if absent
+  const int32_t* pos_csc;         // [N*N] full -> CSC value index, -1 if absent
+};
+
+}  // namespace pj
+
+struct pj_mech {
+  int32_t ns = 0, nr = 0, nnz = 0;
+  int device = -1;
+  // host copies of the description
+  std::vector<double> W, T_mid, nasa_low, nasa_high, A, beta, Ea, A0, beta0, Ea0, troe, sri, eff_val;
+  std::vector<int32_t> kind, rev, reac_sp, reac_nu, prod_sp, prod_nu, troe_n, eff_ptr, eff_sp;
+  // derived
+  std::vector<int32_t> perm;          // kernel order -> original reaction index
+  std::vector<int32_t> csr_ptr, csr_idx, csc_ptr, csc_idx;
+  std::vector<int32_t> pos_csr, pos_csc;
+  pj::DevMech dm{};
+  void* dev_blob = nullptr;
+  size_t dev_bytes = 0;
+};
+
+namespace pj {
+// error reporting (thread-local message)
+int fail(int code, const std::string& msg);
+int check_cuda(int err, const char* what);
+int mech_build(pj_mech* m);          // pack + pattern + upload
+void mech_release(pj_mech* m);
+}  // namespace pj

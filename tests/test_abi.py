@@ -1,0 +1,139 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/pyjac_gb.h, builds the exact sparsity pattern and rejects
+bad arguments with the documented codes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1809_01029_gb300 as pj
+from paper_1809_01029_gb300 import _native as N
+from tests import tiny_mechs as tm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_01029_gb300 import build
+    build.build()
+    return N.load()
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pj_\w+)\s*\(", src, re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_every_declared_symbol_has_a_binding_signature(lib):
+    missing = [n for n in declared_symbols() if n not in N.SIGNATURES]
+    assert not missing, missing
+
+
+def test_version(lib):
+    assert b"pyjac_gb" in lib.pj_version()
+
+
+@pytest.mark.parametrize("name", ["h2co13", "gri53", "usc111"])
+def test_pattern_bit_exact_against_oracle(lib, mechs, name):
+    m = mechs(name)
+    h = pj.pj_mech_create(m)
+    for fmt, ref in ((pj.PJ_CSR, oracle.csr_pattern(m)), (pj.PJ_CSC, oracle.csc_pattern(m))):
+        ptr, idx = h.sparsity(fmt)
+        assert ptr.tobytes() == ref[0].astype(np.int32).tobytes()
+        assert idx.tobytes() == ref[1].astype(np.int32).tobytes()
+
+
+@pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency"])
+def test_pattern_tiny_mechanisms(lib, mk):
+    m = getattr(tm, mk)()
+    h = pj.pj_mech_create(m)
+    ptr, idx = h.sparsity(pj.PJ_CSR)
+    rp, ci = oracle.csr_pattern(m)
+    assert np.array_equal(ptr, rp) and np.array_equal(idx, ci)
+
+
+def test_mechanism_file_round_trip(lib, mechs, tmp_path):
+    m = mechs("gri53")
+    path = str(tmp_path / "gri53.pjmech")
+    synth.write_mechanism(m, path)
+    back = synth.read_mechanism(path)
+    for f in ("W", "nasa_low", "nasa_high", "A", "beta", "Ea", "A0", "troe", "sri", "eff_val"):
+        assert np.array_equal(getattr(m, f), getattr(back, f)), f
+    h1 = pj.pj_mech_create(m)
+    h2 = pj.pj_mech_load(path)
+    assert (h1.n_species, h1.n_reactions, h1.nnz) == (h2.n_species, h2.n_reactions, h2.nnz)
+    for fmt in (pj.PJ_CSR, pj.PJ_CSC):
+        a, b = h1.sparsity(fmt), h2.sparsity(fmt)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_corrupt_mechanism_file(lib, tmp_path, mechs):
+    path = str(tmp_path / "bad.pjmech")
+    synth.write_mechanism(mechs("h2co13"), path)
+    txt = open(path).read().split("\n")
+    open(path, "w").write("\n".join(txt[: len(txt) // 2]))
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_mech_load(path)
+    assert e.value.code == N.PJ_ERR_MECH
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_mech_load(str(tmp_path / "missing"))
+    assert e.value.code == N.PJ_ERR_ARG
+
+
+def test_invalid_mechanisms_rejected(lib):
+    base = tm.all_kinds()
+    cases = []
+    m = base.copy(); m.A = m.A.copy(); m.A[0] = -1.0; cases.append(m)
+    m = base.copy(); m.reac_sp = m.reac_sp.copy(); m.reac_sp[0, 0] = 99; cases.append(m)
+    m = base.copy(); m.kind = m.kind.copy(); m.kind[0] = 9; cases.append(m)
+    m = base.copy(); m.troe_n = m.troe_n.copy(); m.troe_n[int(np.flatnonzero(m.kind == synth.TROE)[0])] = 5
+    cases.append(m)
+    for bad in cases:
+        with pytest.raises(pj.PJError) as e:
+            pj.pj_mech_create(bad)
+        assert e.value.code == N.PJ_ERR_MECH
+
+
+def test_argument_errors(lib):
+    h = pj.pj_mech_create(tm.all_kinds())
+    f = lib.pj_eval_source_terms
+    p = C.c_void_p(16)
+    assert f(None, 0, 1, p, p, 1, p, None, None, 0, None) == N.PJ_ERR_ARG
+    assert f(h.handle, 7, 1, p, p, 1, p, None, None, 0, None) == N.PJ_ERR_ARG
+    assert f(h.handle, 0, 4, p, p, 2, p, None, None, 0, None) == N.PJ_ERR_ARG       # ld < n
+    assert f(h.handle, 0, -1, p, p, 2, p, None, None, 0, None) == N.PJ_ERR_ARG
+    assert f(h.handle, 0, 4, None, p, 4, p, None, None, 0, None) == N.PJ_ERR_ARG
+    g = lib.pj_eval_jacobian_sparse
+    assert g(h.handle, 0, 2, 1, p, p, 1, p, None, None, None, 0, None) == N.PJ_ERR_ARG  # fmt
+    assert lib.pj_workspace_size(h.handle, 99, 10, C.byref(C.c_size_t())) == N.PJ_ERR_ARG
+    assert b"fmt" in lib.pj_last_error() or len(lib.pj_last_error()) > 0
+
+
+def test_no_device_means_no_silent_fallback(lib):
+    """Without a GPU the evaluation entry points fail; nothing computes on the host."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("GPU present")
+    except ImportError:
+        pass
+    h = pj.pj_mech_create(tm.all_kinds())
+    p = C.c_void_p(16)
+    rc = lib.pj_eval_source_terms(h.handle, 0, 1, p, p, 1, p, None, None, 0, None)
+    assert rc == N.PJ_ERR_CUDA

@@ -173,6 +173,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--op", default="jac_csr", choices=["jac_csr", "jac_csc", "jac_dense", "source"],
+                    help="what one step evaluates (default: source terms + CSR Jacobian)")
+    ap.add_argument("--mode", default="conp", choices=["conp", "conv"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -194,12 +197,13 @@ def main():
     m = synth.make_mechanism("gri53")
     h = pj.pj_mech_create(m)
     n = args.n
-    mode = synth.CONP
+    mode = synth.CONP if args.mode == "conp" else synth.CONV
     phi_h, par_h = synth.make_states(m, n, 2018 + 2 + 1000 * rank, mode)
     dev = torch.device("cuda", local)
     phi = torch.from_numpy(phi_h).to(dev)
     par = torch.from_numpy(par_h).to(dev)
-    vals = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    N1 = m.n_species + 1
+    vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
     dphi = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -209,7 +213,13 @@ def main():
     work_s = torch.empty(max(wbs, 1), dtype=torch.uint8, device=dev)
 
     def step():
-        pj.pj_eval_jacobian_sparse(h, mode, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)
+        if args.op == "source":
+            pj.pj_eval_source_terms(h, mode, n, par, phi, n, dphi, status, work_s, wbs, stream)
+        elif args.op == "jac_dense":
+            pj.pj_eval_jacobian_dense(h, mode, n, par, phi, n, vals, dphi, status, work, wb, stream)
+        else:
+            fmt = pj.PJ_CSC if args.op == "jac_csc" else pj.PJ_CSR
+            pj.pj_eval_jacobian_sparse(h, mode, fmt, n, par, phi, n, vals, dphi, status, work, wb, stream)
 
     for _ in range(args.warmup):
         step()
@@ -238,18 +248,18 @@ def main():
     assert int(status.item()) == 0, "invalid states in the benchmark batch"
 
     # roofline of the (single) kernel of the step: FP64 pipe
-    fp64_work = fp64_work_per_state(m, jacobian=True)
+    fp64_work = fp64_work_per_state(m, jacobian=args.op != "source")
     achieved = fp64_work * n / (ms * 1e-3) / 1e9     # G DFMA-equivalent / s
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_jacobian<CONP,CSR>", "work_per_state": fp64_work,
+                "kernel": "k_source_terms" if args.op == "source" else "k_jacobian", "work_per_state": fp64_work,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
 
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and args.op == "jac_csr":
         def timeit(fn, reps=3):
             fn()
             torch.cuda.synchronize()
@@ -270,16 +280,16 @@ def main():
             h, synth.CONV, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
         del vals
         torch.cuda.empty_cache()
-        N1 = m.n_species + 1
         jd = torch.empty((N1 * N1, n), dtype=torch.float64, device=dev)
         variants["jacobian_dense_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_dense(
             h, mode, n, par, phi, n, jd, dphi, status, work, wb, stream)) * 1e-3)
         del jd
         torch.cuda.empty_cache()
-        vals = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+        N1 = m.n_species + 1
+    vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.op == "jac_csr":
         # the same step through the public API with HOST buffers: H2D of the
         # states, the kernel, D2H of the Jacobian values and source terms
         phi_pin = torch.from_numpy(phi_h).pin_memory()
@@ -321,7 +331,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mechanism": "synthetic 53 species / 325 reactions (seed 1811)",
-                       "states_per_gpu": n, "mode": "CONP", "output": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
+                       "states_per_gpu": n, "mode": args.mode.upper(), "op": args.op,
+                       "output": {"jac_csr": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
+                                  "jac_csc": "source terms + CSC Jacobian (nnz %d)" % h.nnz,
+                                  "jac_dense": "source terms + dense Jacobian (%d entries)" % (N1 * N1),
+                                  "source": "source terms"}[args.op],
                        "l2": "inputs and outputs larger than L2 (%.1f GB per step)" % ((h.nnz + 2 * (m.n_species + 1)) * n * 8 / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -167,9 +167,10 @@ int pj_eval_source_terms(const pj_mech* mech, int mode, int64_t n, const double*
 
 /* Exact analytical Jacobian J_ij = d f_i / d Phi_j (Sec. 2.2 "Jacobian
  * arrangement"; sparse storage Sec. 3.3) in CSR (fmt = PJ_CSR) or CSC
- * (PJ_CSC) value order: d_vals[e*ld + s].  d_dphi, if non-NULL, also
- * receives the source terms.  d_work must point to pj_workspace_size() bytes
- * of device memory (may be NULL when that size is 0). */
+ * (PJ_CSC) value order: d_vals[e*ld + s].  d_dphi (required, same layout as
+ * d_phi) receives the source terms, which the Jacobian kernel computes on the
+ * way.  d_work must point to pj_workspace_size(PJ_OP_JACOBIAN) bytes of
+ * device memory (may be NULL when that size is 0). */
 int pj_eval_jacobian_sparse(const pj_mech* mech, int mode, int fmt, int64_t n,
                             const double* d_param, const double* d_phi, int64_t ld,
                             double* d_vals, double* d_dphi, int* d_status,

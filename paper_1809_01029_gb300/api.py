@@ -174,11 +174,18 @@ def source_terms(mech, mode, phi, param, out=None, status=None, stream=None):
     return out
 
 
+def _dphi_like(mech, phi, ld, n):
+    import torch
+    return torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+
+
 def jacobian_sparse(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=None, stream=None):
     import torch
     n, ld = _check_batch(mech, phi, param)
     if out is None:
         out = torch.empty((mech.nnz, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    if dphi is None:
+        dphi = _dphi_like(mech, phi, ld, n)
     work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
     pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, out, dphi, status, work, wb, stream)
     return out
@@ -190,6 +197,8 @@ def jacobian_dense(mech, mode, phi, param, out=None, dphi=None, status=None, str
     N1 = mech.n_species + 1
     if out is None:
         out = torch.empty((N1 * N1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    if dphi is None:
+        dphi = _dphi_like(mech, phi, ld, n)
     work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
     pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, out, dphi, status, work, wb, stream)
     return out

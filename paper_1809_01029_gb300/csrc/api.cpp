@@ -63,6 +63,7 @@ extern "C" int pj_eval_jacobian_sparse(const pj_mech* m, int mode, int fmt, int6
   if (fmt != PJ_CSR && fmt != PJ_CSC) return fail(PJ_ERR_ARG, "pj_eval_jacobian_sparse: fmt must be PJ_CSR or PJ_CSC");
   int rc = check_common("pj_eval_jacobian_sparse", m, mode, n, ld, param, phi, vals);
   if (rc) return rc;
+  if (n > 0 && !dphi) return fail(PJ_ERR_ARG, "pj_eval_jacobian_sparse: d_dphi is required");
   if (n == 0) return PJ_OK;
   return launch_jacobian(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, work, work_bytes,
                          (cudaStream_t)stream);
@@ -73,6 +74,7 @@ extern "C" int pj_eval_jacobian_dense(const pj_mech* m, int mode, int64_t n, con
                                       size_t work_bytes, void* stream) {
   int rc = check_common("pj_eval_jacobian_dense", m, mode, n, ld, param, phi, jac);
   if (rc) return rc;
+  if (n > 0 && !dphi) return fail(PJ_ERR_ARG, "pj_eval_jacobian_dense: d_dphi is required");
   if (n == 0) return PJ_OK;
   return launch_jacobian(m->dm, mode, PJ_DENSE, n, param, phi, ld, jac, dphi, status, work, work_bytes,
                          (cudaStream_t)stream);

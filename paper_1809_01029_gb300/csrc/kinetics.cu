@@ -117,16 +117,145 @@ __device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind,
   return 1.0;  // Lindemann
 }
 
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
+// nu * x with the common nu = +-1 done as a sign flip (integer pipe)
+__device__ __forceinline__ double nu_times(int nu, double nud, double x) {
+  if (nu == 1) return x;
+  if (nu == -1) return dneg(x);
+  return nud * x;
+}
+
+// R = k * prod_a C_a^nu_a over one reaction side (positions off .. off+n-1)
+// and, with DER, dR[a] = dR/dC_a.  The shape code selects the minimal
+// multiply sequence; SH_GEN falls back to a general product.
+template <bool DER>
+__device__ __forceinline__ double side_rate(const StateArrays& A, int aC, const Rxn* __restrict__ r, int off,
+                                            int shape, int n, double k, double (&dR)[PJ_MAX_SP]) {
+  switch (shape) {
+    case SH_1: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off]));
+      if (DER) dR[0] = k;
+      return k * c0;
+    }
+    case SH_2: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off]));
+      const double t = k * c0;
+      if (DER) dR[0] = t + t;
+      return t * c0;
+    }
+    case SH_11: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double t = k * c1;
+      if (DER) {
+        dR[0] = t;
+        dR[1] = k * c0;
+      }
+      return t * c0;
+    }
+    case SH_21: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double t = k * c0;
+      const double t1 = t * c1;
+      if (DER) {
+        dR[0] = t1 + t1;
+        dR[1] = t * c0;
+      }
+      return t1 * c0;
+    }
+    case SH_111: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double c2 = A.at(aC, __ldg(&r->sp[off + 2]));
+      const double t2 = k * c2;
+      const double t12 = t2 * c1;
+      if (DER) {
+        dR[0] = t12;
+        dR[1] = t2 * c0;
+        dR[2] = (k * c0) * c1;
+      }
+      return t12 * c0;
+    }
+    default: {
+      double pw[PJ_MAX_SP], dpw[PJ_MAX_SP];
+#pragma unroll
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        pw[a] = 1.0;
+        dpw[a] = 0.0;
+        if (a < n) {
+          const int v = __ldg(&r->nu[off + a]);
+          const double c = A.at(aC, __ldg(&r->sp[off + a]));
+          const double cm = powi(c, v - 1);
+          pw[a] = cm * c;
+          dpw[a] = v * cm;
+        }
+      }
+      double R = k;
+#pragma unroll
+      for (int a = 0; a < PJ_MAX_SP; a++)
+        if (a < n) R *= pw[a];
+      if (DER) {
+#pragma unroll
+        for (int a = 0; a < PJ_MAX_SP; a++) {
+          if (a >= n) continue;
+          double p = k * dpw[a];
+#pragma unroll
+          for (int b = 0; b < PJ_MAX_SP; b++)
+            if (b != a && b < n) p *= pw[b];
+          dR[a] = p;
+        }
+      }
+      return R;
+    }
+  }
+}
+
+// Forward and reverse rate constants; the two exponentials sit in one basic
+// block so their dependency chains interleave.
+__device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, const Rxn* __restrict__ r, int rev,
+                                               int nre, int npr, double lnkf, double logPRT, double& kf,
+                                               double& kr) {
+  if (rev) {
+    double dg = 0.0;
+#pragma unroll
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre) dg = fma(-__ldg(&r->nud[a]), A.at(aG, __ldg(&r->sp[a])), dg);
+      if (a < npr) dg = fma(__ldg(&r->nud[PJ_MAX_SP + a]), A.at(aG, __ldg(&r->sp[PJ_MAX_SP + a])), dg);
+    }
+    // kr = kf / Kc with Kc = exp(-dg) (P_std / R T)^dnu
+    const double larg = lnkf + dg - __ldg(&r->dnu) * logPRT;
+    kf = exp(lnkf);
+    kr = exp(larg);
+  } else {
+    kf = exp(lnkf);
+    kr = 0.0;
+  }
+}
+
+// Third-body concentration [M] = C_tot + sum_e (alpha_e - 1) C_e.
+__device__ __forceinline__ double third_body(const DevMech& m, const StateArrays& A, int aC, const Rxn* __restrict__ r,
+                                             double Ctot) {
+  double M = Ctot;
+  for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
+    M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
+  return M;
+}
+
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }  // result unused: red.global.add.f64
+
 // ---------------------------------------------------------------------------
 // source terms
 // ---------------------------------------------------------------------------
+// Shared memory holds C_k and g_k/RT per state; production rates are summed
+// by L2 reductions into the output rows (the bath gas in a register).
 template <int MODE>
 __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, const double* __restrict__ param,
                                                       const double* __restrict__ phi, int64_t ld,
                                                       double* __restrict__ out, int* status, double* ws,
                                                       int64_t ws_stride) {
   PJ_DYN_SMEM;
-  const int ns = m.ns;
+  const int ns = m.ns, bath = m.ns - 1;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   StateArrays A;
   A.ns = ns;
@@ -137,7 +266,7 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
     A.base = smem + threadIdx.x;
     A.stride = blockDim.x;
   }
-  enum { aC = 0, aG = 1, aW = 2 };
+  enum { aC = 0, aG = 1 };
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     StateScalars st;
     if (!load_state<MODE>(m, phi, param, ld, s, A, aC, st)) {
@@ -146,45 +275,32 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
       continue;
     }
     const double T = st.T, invT = st.invT, lnT = st.lnT;
+    double* __restrict__ wrow = out + 2 * ld + s;   // wdot_k accumulates at wrow[k*ld]
+    for (int k = 0; k < ns - 1; k++) wrow[(int64_t)k * ld] = 0.0;
     double den = 0.0;
     for (int k = 0; k < ns; k++) {
       double cp, h, sr;
       nasa_eval(nasa_block(m, k, T), T, invT, lnT, cp, h, sr);
       A.at(aG, k) = h - sr;
-      A.at(aW, k) = 0.0;
       den = fma(A.at(aC, k), MODE == PJ_CONP ? cp : cp - 1.0, den);
     }
     den *= RU;
     const double logPRT = m.log_pstd_over_r - lnT;  // ln(P_std / (R T))
+    double w_bath = 0.0;
 
     for (int i = 0; i < m.nr; i++) {
       const Rxn* __restrict__ r = m.rxn + i;
       const int kind = __ldg(&r->kind);
-      const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod);
+      const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod), rev = __ldg(&r->rev);
       const double lnkf = fma(__ldg(&r->beta), lnT, __ldg(&r->lnA)) - __ldg(&r->theta) * invT;
-      double Rf = exp(lnkf);
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++)
-        if (a < nre) Rf *= powi(A.at(aC, __ldg(&r->sp[a])), __ldg(&r->nu[a]));
-      double Rr = 0.0;
-      if (__ldg(&r->rev)) {
-        double dg = 0.0;
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++) {
-          if (a < nre) dg -= __ldg(&r->nu[a]) * A.at(aG, __ldg(&r->sp[a]));
-          if (a < npr) dg += __ldg(&r->nu[PJ_MAX_SP + a]) * A.at(aG, __ldg(&r->sp[PJ_MAX_SP + a]));
-        }
-        // kr = kf / Kc with Kc = exp(-dg) (P_std / R T)^dnu
-        Rr = exp(lnkf + dg - __ldg(&r->dnu) * logPRT);
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++)
-          if (a < npr) Rr *= powi(A.at(aC, __ldg(&r->sp[PJ_MAX_SP + a])), __ldg(&r->nu[PJ_MAX_SP + a]));
-      }
+      double kf, kr;
+      rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+      double dmy[PJ_MAX_SP];
+      const double Rf = side_rate<false>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dmy);
+      const double Rr = rev ? side_rate<false>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dmy) : 0.0;
       double c = 1.0;
       if (kind != PJ_ELEMENTARY) {
-        double M = st.Ctot;
-        for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
-          M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
+        const double M = third_body(m, A, aC, r, st.Ctot);
         if (kind == PJ_THIRD_BODY) {
           c = M;
         } else {
@@ -199,12 +315,16 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
         if (a < nre) {
-          double& w = A.at(aW, __ldg(&r->sp[a]));
-          w = fma(-(double)__ldg(&r->nu[a]), q, w);
+          const int k = __ldg(&r->sp[a]);
+          const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
+          if (k == bath) w_bath -= v;
+          else red_add(wrow + (int64_t)k * ld, dneg(v));
         }
         if (a < npr) {
-          double& w = A.at(aW, __ldg(&r->sp[PJ_MAX_SP + a]));
-          w = fma((double)__ldg(&r->nu[PJ_MAX_SP + a]), q, w);
+          const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
+          const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
+          if (k == bath) w_bath += v;
+          else red_add(wrow + (int64_t)k * ld, v);
         }
       }
     }
@@ -214,11 +334,11 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
     for (int k = 0; k < ns; k++) {
       double cp, h, sr;
       nasa_eval(nasa_block(m, k, T), T, invT, lnT, cp, h, sr);
-      const double wk = A.at(aW, k);
+      const double wk = k < bath ? __ldcg(wrow + (int64_t)k * ld) : w_bath;
       num = fma(MODE == PJ_CONP ? h : h - 1.0, wk, num);
-      if (k < ns - 1) {
+      if (k < bath) {
         Om = fma(__ldg(m.wfac + k), wk, Om);
-        out[(int64_t)(k + 2) * ld + s] = st.V * wk;
+        wrow[(int64_t)k * ld] = st.V * wk;
       }
     }
     num *= RU * T;
@@ -242,9 +362,12 @@ __device__ __forceinline__ int64_t jpos(const DevMech& m, int row, int col) {
 }
 
 __device__ __forceinline__ void jred(double* J, int64_t e, int64_t ld, int64_t s, double v) {
-  if (e >= 0) atomicAdd(J + e * ld + s, v);  // result unused: red.global.add.f64
+  if (e >= 0) red_add(J + e * ld + s, v);
 }
 
+// Shared memory holds C_k, g_k/RT and h_k/RT per state.  Production rates go
+// to the source-term output by L2 reductions (bath gas in a register);
+// Jacobian entries to the zero-initialised output by L2 reductions.
 template <int MODE, int FMT>
 __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const double* __restrict__ param,
                                                   const double* __restrict__ phi, int64_t ld,
@@ -263,7 +386,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     A.base = smem + threadIdx.x;
     A.stride = blockDim.x;
   }
-  enum { aC = 0, aG = 1, aH = 2, aW = 3 };
+  enum { aC = 0, aG = 1, aH = 2 };
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     StateScalars st;
     if (!load_state<MODE>(m, phi, param, ld, s, A, aC, st)) {
@@ -273,8 +396,10 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       continue;
     }
     const double T = st.T, V = st.V, P = st.P, invT = st.invT, lnT = st.lnT, Ctot = st.Ctot;
-    const double invT2 = invT * invT;
+    const double invT2 = invT * invT, invV = 1.0 / V;
     for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = 0.0;
+    double* __restrict__ wrow = dphi + 2 * ld + s;  // wdot_k accumulates at wrow[k*ld]
+    for (int k = 0; k < ns - 1; k++) wrow[(int64_t)k * ld] = 0.0;
 
     // thermo, energy-equation denominator D = sum_k C_k Cx_k and dD/dT
     double den = 0.0, dden_T = 0.0, Cx_bath = 0.0;
@@ -285,7 +410,6 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       nasa_cp(cb, T, cp2, dcp);
       A.at(aG, k) = h - sr;
       A.at(aH, k) = h;
-      A.at(aW, k) = 0.0;
       const double Ck = A.at(aC, k);
       const double cx = MODE == PJ_CONP ? cp : cp - 1.0;
       den = fma(Ck, cx, den);
@@ -296,14 +420,14 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     const double C_bath = A.at(aC, bath);
     // derivatives of the bath-gas concentration
     const double dCb_T = -Ctot * invT;
-    const double dCb_S = MODE == PJ_CONP ? (Ctot - C_bath) / V : Ctot / P;
+    const double dCb_S = MODE == PJ_CONP ? (Ctot - C_bath) * invV : Ctot / P;
     dden_T = RU * dden_T + Cx_bath * dCb_T;
-    const double dden_S = MODE == PJ_CONP ? (Cx_bath * Ctot - den) / V : Cx_bath * Ctot / P;
+    const double dden_S = MODE == PJ_CONP ? (Cx_bath * Ctot - den) * invV : Cx_bath * Ctot / P;
     const double logPRT = m.log_pstd_over_r - lnT;
 
     // accumulators of the energy row (T) and state row (S) for the T and S
     // columns and for the part common to every species column
-    double AT_T = 0, AT_S = 0, AS_T = 0, AS_S = 0, ATB = 0, ASB = 0;
+    double AT_T = 0, AT_S = 0, AS_T = 0, AS_S = 0, ATB = 0, ASB = 0, w_bath = 0;
 
     for (int i = 0; i < m.nr; i++) {
       const Rxn* __restrict__ r = m.rxn + i;
@@ -312,88 +436,31 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       const int rev = __ldg(&r->rev);
       const double beta = __ldg(&r->beta), theta = __ldg(&r->theta);
       const double lnkf = fma(beta, lnT, __ldg(&r->lnA)) - theta * invT;
-      const double kf = exp(lnkf);
       const double dlnkf = fma(theta, invT2, beta * invT);
-
-      // forward concentration product and its partial derivatives
-      int sp[2 * PJ_MAX_SP];
-      double dR[2 * PJ_MAX_SP];
-      double pw[PJ_MAX_SP], dpw[PJ_MAX_SP];
-      double dh = 0.0, dg = 0.0;
+      double kf, kr;
+      rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+      double dh = 0.0;
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
-        sp[a] = a < nre ? __ldg(&r->sp[a]) : -1;
-        sp[PJ_MAX_SP + a] = a < npr ? __ldg(&r->sp[PJ_MAX_SP + a]) : -1;
-        pw[a] = 1.0;
-        dpw[a] = 0.0;
-        if (a < nre) {
-          const int v = __ldg(&r->nu[a]);
-          const double c = A.at(aC, sp[a]);
-          const double cm = powi(c, v - 1);
-          pw[a] = cm * c;
-          dpw[a] = v * cm;
-          dh -= v * A.at(aH, sp[a]);
-          dg -= v * A.at(aG, sp[a]);
-        }
-        if (a < npr) {
-          const int v = __ldg(&r->nu[PJ_MAX_SP + a]);
-          dh += v * A.at(aH, sp[PJ_MAX_SP + a]);
-          dg += v * A.at(aG, sp[PJ_MAX_SP + a]);
-        }
+        if (a < nre) dh = fma(-__ldg(&r->nud[a]), A.at(aH, __ldg(&r->sp[a])), dh);
+        if (a < npr) dh = fma(__ldg(&r->nud[PJ_MAX_SP + a]), A.at(aH, __ldg(&r->sp[PJ_MAX_SP + a])), dh);
       }
-      double Rf = kf;
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++) Rf *= pw[a];
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++) {
-        double p = kf * dpw[a];
-#pragma unroll
-        for (int b = 0; b < PJ_MAX_SP; b++)
-          if (b != a) p *= pw[b];
-        dR[a] = p;
-      }
+      double dRf[PJ_MAX_SP], dRr[PJ_MAX_SP];
+      const double Rf = side_rate<true>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dRf);
       double Rr = 0.0, dlnkr = 0.0;
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++) dR[PJ_MAX_SP + a] = 0.0;
       if (rev) {
-        const double dnu = __ldg(&r->dnu);
-        const double kr = exp(lnkf + dg - dnu * logPRT);
-        dlnkr = dlnkf - (dh - dnu) * invT;
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++) {
-          pw[a] = 1.0;
-          dpw[a] = 0.0;
-          if (a < npr) {
-            const int v = __ldg(&r->nu[PJ_MAX_SP + a]);
-            const double c = A.at(aC, sp[PJ_MAX_SP + a]);
-            const double cm = powi(c, v - 1);
-            pw[a] = cm * c;
-            dpw[a] = v * cm;
-          }
-        }
-        Rr = kr;
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++) Rr *= pw[a];
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++) {
-          double p = kr * dpw[a];
-#pragma unroll
-          for (int b = 0; b < PJ_MAX_SP; b++)
-            if (b != a) p *= pw[b];
-          dR[PJ_MAX_SP + a] = -p;  // derivative of -Rr
-        }
+        Rr = side_rate<true>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dRr);
+        dlnkr = dlnkf - (dh - __ldg(&r->dnu)) * invT;
       }
       const double Rn = Rf - Rr;
 
       // pressure modification c and its derivatives
       double c = 1.0, dcdT = 0.0, dcdS = 0.0, dcdM = 0.0;
       if (kind != PJ_ELEMENTARY) {
-        double M = Ctot;
-        for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
-          M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
+        const double M = third_body(m, A, aC, r, Ctot);
         const double ab = __ldg(&r->alpha_bath);
         const double dMdT = ab * dCb_T;
-        const double dMdS = MODE == PJ_CONP ? (ab * Ctot - M) / V : ab * Ctot / P;
+        const double dMdS = MODE == PJ_CONP ? (ab * Ctot - M) * invV : ab * Ctot / P;
         if (kind == PJ_THIRD_BODY) {
           c = M;
           dcdM = 1.0;
@@ -423,13 +490,24 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       double dRdT = Rf * dlnkf - Rr * dlnkr;
       double dRdS = 0.0;
 #pragma unroll
-      for (int a = 0; a < 2 * PJ_MAX_SP; a++) {
-        if (sp[a] < 0) continue;
-        if (sp[a] == bath) {
-          dRdT = fma(dR[a], dCb_T, dRdT);
-          dRdS = fma(dR[a], dCb_S, dRdS);
-        } else if (MODE == PJ_CONP) {
-          dRdS = fma(dR[a], -A.at(aC, sp[a]) / V, dRdS);
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        if (a < nre) {
+          const int k = __ldg(&r->sp[a]);
+          if (k == bath) {
+            dRdT = fma(dRf[a], dCb_T, dRdT);
+            dRdS = fma(dRf[a], dCb_S, dRdS);
+          } else if (MODE == PJ_CONP) {
+            dRdS = fma(dRf[a], -A.at(aC, k) * invV, dRdS);
+          }
+        }
+        if (rev && a < npr) {
+          const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
+          if (k == bath) {
+            dRdT = fma(-dRr[a], dCb_T, dRdT);
+            dRdS = fma(-dRr[a], dCb_S, dRdS);
+          } else if (MODE == PJ_CONP) {
+            dRdS = fma(dRr[a], A.at(aC, k) * invV, dRdS);
+          }
         }
       }
       const double q = c * Rn;
@@ -438,12 +516,16 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
         if (a < nre) {
-          double& w = A.at(aW, sp[a]);
-          w = fma(-(double)__ldg(&r->nu[a]), q, w);
+          const int k = __ldg(&r->sp[a]);
+          const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
+          if (k == bath) w_bath -= v;
+          else red_add(wrow + (int64_t)k * ld, dneg(v));
         }
         if (a < npr) {
-          double& w = A.at(aW, sp[PJ_MAX_SP + a]);
-          w = fma((double)__ldg(&r->nu[PJ_MAX_SP + a]), q, w);
+          const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
+          const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
+          if (k == bath) w_bath += v;
+          else red_add(wrow + (int64_t)k * ld, v);
         }
       }
 
@@ -459,8 +541,8 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       const double VdqdT = V * dqdT, VdqdS = V * dqdS;
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
-        jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, rn.nu * VdqdT);
-        jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, rn.nu * VdqdS);
+        jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times(rn.nu, rn.nud, VdqdT));
+        jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times(rn.nu, rn.nud, VdqdS));
       }
 
       // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i
@@ -472,14 +554,16 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
         }
         for (int q2 = row_lo; q2 < row_hi; q2++) {
           const RowNu rn = m.rows[q2];
-          jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, rn.nu * val);
+          jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times(rn.nu, rn.nud, val));
         }
         jred(J, jpos<FMT>(m, 0, j + 2), ld, s, dE * val);
         jred(J, jpos<FMT>(m, 1, j + 2), ld, s, dW * val);
       };
 #pragma unroll
-      for (int a = 0; a < 2 * PJ_MAX_SP; a++)
-        if (sp[a] >= 0 && (a < PJ_MAX_SP || rev)) slot(sp[a], c * dR[a]);
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        if (a < nre) slot(__ldg(&r->sp[a]), c * dRf[a]);
+        if (rev && a < npr) slot(__ldg(&r->sp[PJ_MAX_SP + a]), dneg(c * dRr[a]));
+      }
       if (kind != PJ_ELEMENTARY) {
         const double t = Rn * dcdM;
         for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
@@ -488,7 +572,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       if (__ldg(&r->dense)) {
         for (int q2 = row_lo; q2 < row_hi; q2++) {
           const RowNu rn = m.rows[q2];
-          const double v = rn.nu * Bi;
+          const double v = nu_times(rn.nu, rn.nud, Bi);
           for (int j = 0; j < ns - 1; j++) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
         }
         ATB = fma(dE, Bi, ATB);
@@ -503,26 +587,25 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       nasa_cp(nasa_block(m, k, T), T, cp, dcp);
       const double cx = RU * (MODE == PJ_CONP ? cp : cp - 1.0);
       A.at(aG, k) = cx;
-      const double wk = A.at(aW, k);
+      const double wk = k < bath ? __ldcg(wrow + (int64_t)k * ld) : w_bath;
       num = fma(MODE == PJ_CONP ? A.at(aH, k) : A.at(aH, k) - 1.0, wk, num);
       sumCxW = fma(cx, wk, sumCxW);
-      if (k < ns - 1) {
+      if (k < bath) {
         Om = fma(__ldg(m.wfac + k), wk, Om);
-        if (dphi) dphi[(int64_t)(k + 2) * ld + s] = V * wk;
+        wrow[(int64_t)k * ld] = V * wk;
         if (MODE == PJ_CONP) jred(J, jpos<FMT>(m, k + 2, 1), ld, s, wk);
       }
     }
     num *= RU * T;
     const double Tdot = -num / den;
     const double Sdot = MODE == PJ_CONP ? V * Tdot * invT + (RU * T * V / P) * Om : P * Tdot * invT + RU * T * Om;
-    if (dphi) {
-      dphi[s] = Tdot;
-      dphi[ld + s] = Sdot;
-    }
+    dphi[s] = Tdot;
+    dphi[ld + s] = Sdot;
 
     // energy row 0 and state row 1
     const double iden = 1.0 / den;
     const double Cx_b = A.at(aG, bath);
+    const double rtvp = MODE == PJ_CONP ? RU * T * V / P : RU * T;
     for (int j = 0; j < N; j++) {
       const int64_t e0 = jpos<FMT>(m, 0, j), e1 = jpos<FMT>(m, 1, j);
       double jT, dOm;
@@ -535,16 +618,16 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       } else {
         const double accT = __ldcg(J + e0 * ld + s);
         const double accS = __ldcg(J + e1 * ld + s);
-        jT = -((accT + ATB) / V + Tdot * (A.at(aG, j - 2) - Cx_b) / V) * iden;
-        dOm = (accS + ASB) / V;
+        jT = -(accT + ATB + Tdot * (A.at(aG, j - 2) - Cx_b)) * (invV * iden);
+        dOm = (accS + ASB) * invV;
       }
       double jS;
       if (MODE == PJ_CONP) {
-        jS = (V * invT) * jT + (RU * T * V / P) * dOm;
+        jS = (V * invT) * jT + rtvp * dOm;
         if (j == 0) jS += -V * Tdot * invT2 + (RU * V / P) * Om;
         if (j == 1) jS += Tdot * invT + (RU * T / P) * Om;
       } else {
-        jS = (P * invT) * jT + RU * T * dOm;
+        jS = (P * invT) * jT + rtvp * dOm;
         if (j == 0) jS += -P * Tdot * invT2 + RU * Om;
         if (j == 1) jS += Tdot * invT;
       }
@@ -583,11 +666,14 @@ static int num_sms() {
 // workspace with a fixed grid-stride grid.
 LaunchPlan plan_for(int arrays, int ns, int64_t n) {
   LaunchPlan p{};
-  p.tpb = 128;
   const size_t per_thread = (size_t)arrays * ns * sizeof(double);
   const size_t smem_cap = 227 * 1024;  // opt-in dynamic shared memory per block on sm_100-class parts
-  if (per_thread * p.tpb <= smem_cap) {
+  // threads per SM that fit the per-state arrays in shared memory, as whole
+  // warps; blocks of up to 128 threads so several can share an SM
+  const int fit = (int)((smem_cap / per_thread) / 32 * 32);
+  if (fit >= 128) {
     p.global_ws = false;
+    p.tpb = fit >= 256 ? 128 : (fit % 64 == 0 ? 64 : 32);
     p.smem = per_thread * p.tpb;
     const int64_t blocks = (n + p.tpb - 1) / p.tpb;
     p.grid = (int)(blocks < 1 ? 1 : blocks);
@@ -595,6 +681,7 @@ LaunchPlan plan_for(int arrays, int ns, int64_t n) {
     p.ws_stride = 0;
   } else {
     p.global_ws = true;
+    p.tpb = 128;
     p.smem = 0;
     const int64_t cap = (int64_t)num_sms() * 4;
     const int64_t blocks = (n + p.tpb - 1) / p.tpb;
@@ -605,8 +692,8 @@ LaunchPlan plan_for(int arrays, int ns, int64_t n) {
   return p;
 }
 
-int source_arrays() { return 3; }
-int jacobian_arrays() { return 4; }
+int source_arrays() { return 2; }
+int jacobian_arrays() { return 3; }
 
 template <typename K>
 static int set_smem(K kern, size_t smem) {

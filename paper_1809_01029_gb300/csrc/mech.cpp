@@ -222,17 +222,27 @@ int mech_build(pj_mech* m) {
       r.fp[0] = s[0]; r.fp[1] = s[1]; r.fp[2] = 1.0 / s[2]; r.fp[3] = s[3]; r.fp[4] = s[4];
     }
     for (int a = 0; a < 2 * PJ_MAX_SP; a++) r.sp[a] = -1;
-    for (int a = 0; a < PJ_MAX_SP; a++) {
-      if (m->reac_sp[i * PJ_MAX_SP + a] >= 0) {
-        r.sp[r.nreac] = m->reac_sp[i * PJ_MAX_SP + a];
-        r.nu[r.nreac] = m->reac_nu[i * PJ_MAX_SP + a];
-        r.nreac++;
+    for (int side = 0; side < 2; side++) {
+      const int32_t* ssp = side ? &m->prod_sp[i * PJ_MAX_SP] : &m->reac_sp[i * PJ_MAX_SP];
+      const int32_t* snu = side ? &m->prod_nu[i * PJ_MAX_SP] : &m->reac_nu[i * PJ_MAX_SP];
+      std::vector<std::pair<int, int>> mem;  // (nu, species)
+      for (int a = 0; a < PJ_MAX_SP; a++)
+        if (ssp[a] >= 0) mem.push_back({snu[a], ssp[a]});
+      // larger coefficients first, so 2A + B maps onto SH_21
+      std::stable_sort(mem.begin(), mem.end(), [](auto x, auto y) { return x.first > y.first; });
+      int32_t shape = SH_GEN;
+      if (mem.size() == 1 && mem[0].first == 1) shape = SH_1;
+      else if (mem.size() == 1 && mem[0].first == 2) shape = SH_2;
+      else if (mem.size() == 2 && mem[0].first == 1 && mem[1].first == 1) shape = SH_11;
+      else if (mem.size() == 2 && mem[0].first == 2 && mem[1].first == 1) shape = SH_21;
+      else if (mem.size() == 3 && mem[0].first == 1 && mem[1].first == 1 && mem[2].first == 1) shape = SH_111;
+      r.shape[side] = shape;
+      for (size_t a = 0; a < mem.size(); a++) {
+        r.sp[side * PJ_MAX_SP + a] = mem[a].second;
+        r.nu[side * PJ_MAX_SP + a] = mem[a].first;
+        r.nud[side * PJ_MAX_SP + a] = (double)mem[a].first;
       }
-      if (m->prod_sp[i * PJ_MAX_SP + a] >= 0) {
-        r.sp[PJ_MAX_SP + r.nprod] = m->prod_sp[i * PJ_MAX_SP + a];
-        r.nu[PJ_MAX_SP + r.nprod] = m->prod_nu[i * PJ_MAX_SP + a];
-        r.nprod++;
-      }
+      (side ? r.nprod : r.nreac) = (int32_t)mem.size();
     }
     std::vector<int> nu = net_nu(m, i);
     double dnu = 0, dW = 0;
@@ -255,7 +265,7 @@ int mech_build(pj_mech* m) {
     r.eff_hi = (int32_t)eff_sp.size();
     r.row_lo = (int32_t)rows.size();
     for (int k = 0; k < bath; k++)
-      if (nu[k] != 0) rows.push_back(RowNu{k, nu[k]});
+      if (nu[k] != 0) rows.push_back(RowNu{k, nu[k], (double)nu[k]});
     r.row_hi = (int32_t)rows.size();
     r.dense = rate_dependence(m, i, dep) ? 1 : 0;
   }

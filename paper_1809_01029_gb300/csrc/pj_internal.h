@@ -23,6 +23,18 @@ constexpr double LN10 = 2.302585092994045684;
 //   [14]    T_mid (same in both ranges), [15] unused
 constexpr int NASA_STRIDE = 32;
 
+// Stoichiometric pattern of one reaction side, chosen on the host so that the
+// kernels form C-products and their derivatives with exactly the multiplies
+// they need (species ordered to match the pattern).
+enum : int32_t {
+  SH_1 = 0,    // A
+  SH_2 = 1,    // 2A
+  SH_11 = 2,   // A + B
+  SH_21 = 3,   // 2A + B
+  SH_111 = 4,  // A + B + C
+  SH_GEN = 5   // anything else (generic loop)
+};
+
 // One reaction, packed for warp-uniform loads (every thread of a warp reads
 // the same record).  Reactions are stored in kernel order (see perm).
 struct alignas(16) Rxn {
@@ -32,8 +44,10 @@ struct alignas(16) Rxn {
   double dW;                      // sum_{k<Ns-1} nu_k (1 - W_k/W_Ns)
   double alpha_bath;              // third-body efficiency of the bath gas
   double fp[5];                   // Troe: a, 1/T3, 1/T1, T2, has_T2 ; SRI: a, b, 1/c, d, e
+  double nud[2 * PJ_MAX_SP];      // stoichiometric coefficients as doubles
   int32_t kind, rev;
   int32_t nreac, nprod;
+  int32_t shape[2];               // SH_* of the reactant and product sides
   int32_t sp[2 * PJ_MAX_SP];      // reactants [0, nreac), products [PJ_MAX_SP, PJ_MAX_SP + nprod)
   int32_t nu[2 * PJ_MAX_SP];
   int32_t eff_lo, eff_hi;         // non-default efficiencies in eff_sp / eff_am1
@@ -45,6 +59,7 @@ struct alignas(16) Rxn {
 struct RowNu {
   int32_t k;      // species index (< Ns-1)
   int32_t nu;     // net stoichiometric coefficient
+  double nud;     // the same as a double
 };
 
 // Kernel view of a mechanism (POD, passed by value).

@@ -147,3 +147,16 @@ def test_sharding_by_offset_equals_one_launch(pj, mechs):
     for lo, hi in ((0, 333), (333, 640), (640, 1000)):
         parts.append(pj.jacobian_sparse(h, synth.CONP, d_phi[:, lo:hi], d_par[lo:hi]))
     assert torch.equal(whole, torch.cat(parts, dim=1))
+
+
+def test_jacobian_requires_source_term_buffer(pj, mechs):
+    import torch
+    from paper_1809_01029_gb300 import _native as N
+    m = mechs("h2co13")
+    h = pj.pj_mech_create(m)
+    phi, par = synth.make_states(m, 8, 1, synth.CONP)
+    d_phi, d_par = to_dev(phi), to_dev(par)
+    vals = torch.empty((h.nnz, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, 8, d_par, d_phi, 8, vals, None)
+    assert e.value.code == N.PJ_ERR_ARG

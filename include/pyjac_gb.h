@@ -181,6 +181,25 @@ int pj_eval_jacobian_dense(const pj_mech* mech, int mode, int64_t n, const doubl
                            const double* d_phi, int64_t ld, double* d_jac, double* d_dphi,
                            int* d_status, void* d_work, size_t work_bytes, void* stream);
 
+/* Allocation-free variant of pj_eval_jacobian_sparse (no counterpart in the
+ * paper).  For callers that cannot allocate device memory or call an
+ * allocating library routine, and so cannot supply d_work: the per-state
+ * working arrays live in a fixed 64 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Same arguments and outputs as pj_eval_jacobian_sparse minus the workspace.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress, with the device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents; calls that overlap on the GPU (different streams, or
+ *    concurrent host threads) race on it, so serialise them.
+ *  - Mechanisms whose arrays for 128 states exceed 64 MiB (about 21,800
+ *    species) are rejected with PJ_ERR_UNSUPPORTED; n is unrestricted
+ *    (states are processed in a grid-stride loop). */
+int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int64_t n,
+                                    const double* d_param, const double* d_phi, int64_t ld,
+                                    double* d_vals, double* d_dphi, int* d_status, void* stream);
+
 /* operation ids for pj_workspace_size */
 #define PJ_OP_SOURCE 0
 #define PJ_OP_JACOBIAN 1

@@ -46,6 +46,8 @@ SIGNATURES = {
     "pj_eval_jacobian_dense": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp,
                                          _vp, C.c_size_t, _vp]),
     "pj_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
+    "pj_eval_jacobian_sparse_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
+                                                  _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -142,6 +142,15 @@ def pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, jac, dphi=None, status
                  "pj_eval_jacobian_dense")
 
 
+def pj_eval_jacobian_sparse_noalloc(mech, mode, fmt, n, param, phi, ld, vals, dphi, status=None, stream=None):
+    """Sparse Jacobian without a workspace argument, for callers that cannot
+    allocate device memory: the library's fixed per-device scratch array is
+    used instead (calls overlapping on the GPU race on it)."""
+    return check(N.load().pj_eval_jacobian_sparse_noalloc(mech.handle, mode, fmt, n, _ptr(param), _ptr(phi), ld,
+                                                           _ptr(vals), _ptr(dphi), _ptr(status), _stream(stream)),
+                 "pj_eval_jacobian_sparse_noalloc")
+
+
 # ---------------------------------------------------------------------------
 # convenience wrappers (torch tensors in, torch tensors out)
 # ---------------------------------------------------------------------------

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpyjac_gb.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mech.cpp", "api.cpp", "kinetics.cu", "forms.cu", "batch.cu", "hostio.cpp"]
+SOURCES = ["mech.cpp", "api.cpp", "kinetics.cu", "noalloc.cu", "forms.cu", "batch.cu", "hostio.cpp"]
 
 
 def nvcc() -> str:

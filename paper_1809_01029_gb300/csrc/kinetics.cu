@@ -748,6 +748,31 @@ int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double
 }
 
 size_t workspace_bytes(int arrays, int ns, int64_t n) { return plan_for(arrays, ns, n).ws_bytes; }
+
+// Run k_jacobian with its per-state arrays in a scratch region that holds
+// `scratch_threads` threads' arrays (grid-stride over the states).  Used by
+// the allocation-free entry point (noalloc.cu).
+int launch_jacobian_on_scratch(const DevMech& m, int mode, int fmt, int64_t n, const double* param,
+                               const double* phi, int64_t ld, double* J, double* dphi, int* status,
+                               double* scratch, int64_t scratch_threads, cudaStream_t st) {
+  LaunchPlan p{};
+  p.tpb = 128;
+  p.global_ws = true;
+  p.smem = 0;
+  const int64_t blocks = (n + p.tpb - 1) / p.tpb;
+  int64_t cap = scratch_threads / p.tpb;
+  const int64_t sm_cap = (int64_t)num_sms() * 4;
+  if (cap > sm_cap) cap = sm_cap;
+  p.grid = (int)(blocks < cap ? (blocks < 1 ? 1 : blocks) : cap);
+  p.ws_stride = (int64_t)p.grid * p.tpb;
+  p.ws_bytes = (size_t)jacobian_arrays() * m.ns * sizeof(double) * (size_t)p.ws_stride;
+  if (mode == PJ_CONP) {
+    if (fmt == PJ_CSR) return launch_jac_t<PJ_CONP, PJ_CSR>(m, p, n, param, phi, ld, J, dphi, status, scratch, st);
+    return launch_jac_t<PJ_CONP, PJ_CSC>(m, p, n, param, phi, ld, J, dphi, status, scratch, st);
+  }
+  if (fmt == PJ_CSR) return launch_jac_t<PJ_CONV, PJ_CSR>(m, p, n, param, phi, ld, J, dphi, status, scratch, st);
+  return launch_jac_t<PJ_CONV, PJ_CSC>(m, p, n, param, phi, ld, J, dphi, status, scratch, st);
+}
 #endif  // PJ_NO_LAUNCHERS
 
 }  // namespace pj

@@ -1,0 +1,80 @@
+// Allocation-free sparse Jacobian entry point.
+//
+// The regular entry points take their scratch (the per-state working arrays
+// of large mechanisms) from a caller-provided workspace.  Some callers cannot
+// provide one: code that may not call cudaMalloc or any allocating routine
+// (for instance a solver inside a region whose device memory is owned and
+// fixed by a host application, or host code that is not allowed to touch the
+// CUDA allocator at that point).  For them this file keeps the scratch in a
+// file-scope device array of fixed size that every GPU loading the library
+// holds until the process exits, and exposes one entry point that allocates
+// nothing.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "pj_internal.h"
+
+namespace pj {
+int check_common(const char* fn, const pj_mech* m, int mode, int64_t n, int64_t ld, const void* param,
+                 const void* phi, const void* out);
+int launch_jacobian_on_scratch(const DevMech& m, int mode, int fmt, int64_t n, const double* param,
+                               const double* phi, int64_t ld, double* J, double* dphi, int* status,
+                               double* scratch, int64_t scratch_threads, cudaStream_t st);
+int jacobian_arrays();
+}  // namespace pj
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB per device
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) double g_noalloc_scratch[kScratchBytes / sizeof(double)];
+
+std::mutex g_setup_mutex;
+double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on device `dev` (which must be
+// current).  Looked up once per device; the host-side symbol is only a
+// stand-in and must never be passed to a kernel.
+int scratch_address(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return pj::fail(PJ_ERR_UNSUPPORTED, "pj_eval_jacobian_sparse_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return pj::check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return PJ_OK;
+}
+
+}  // namespace
+
+using namespace pj;
+
+extern "C" int pj_eval_jacobian_sparse_noalloc(const pj_mech* m, int mode, int fmt, int64_t n, const double* param,
+                                               const double* phi, int64_t ld, double* vals, double* dphi,
+                                               int* status, void* stream) {
+  const char* fn = "pj_eval_jacobian_sparse_noalloc";
+  if (fmt != PJ_CSR && fmt != PJ_CSC) return fail(PJ_ERR_ARG, std::string(fn) + ": fmt must be PJ_CSR or PJ_CSC");
+  int rc = check_common(fn, m, mode, n, ld, param, phi, vals);
+  if (rc) return rc;
+  if (n > 0 && !dphi) return fail(PJ_ERR_ARG, std::string(fn) + ": d_dphi is required");
+  if (n == 0) return PJ_OK;
+  const size_t per_thread = (size_t)jacobian_arrays() * m->ns * sizeof(double);
+  const int64_t threads = (int64_t)(kScratchBytes / per_thread) / 128 * 128;
+  if (threads < 128)
+    return fail(PJ_ERR_UNSUPPORTED, std::string(fn) + ": mechanism too large for the fixed scratch (" +
+                                        std::to_string(per_thread * 128) + " bytes needed per 128 states, " +
+                                        std::to_string(kScratchBytes) + " bytes available)");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return check_cuda(e, "cudaGetDevice");
+  double* scratch = nullptr;
+  if ((rc = scratch_address(dev, &scratch))) return rc;
+  return launch_jacobian_on_scratch(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, scratch, threads,
+                                    (cudaStream_t)stream);
+}

@@ -139,6 +139,73 @@ def oracle_baseline(m, mode, n_sample, seed):
     return n_sample / dt, dt
 
 
+def _time(torch, stream, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def other_workloads(pj, synth, torch, dev, stream):
+    """States/s of the other measured cases (one launch per evaluation)."""
+    out = {}
+    # 13 species / 27 reactions, 4096 states: source terms + CSR Jacobian
+    m = synth.make_mechanism("h2co13")
+    h = pj.pj_mech_create(m)
+    n = 4096
+    phi_h, par_h = synth.make_states(m, n, 2018 + 1, synth.CONP)
+    phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+    v = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    t = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, v, f,
+                                                                None, None, 0, stream), reps=20)
+    out["h2co13_4k_jacobian_csr"] = n / (t * 1e-3)
+    # 111 species / 784 reactions, 262,144 states: FP32 Newton matrix vs FP64 Jacobian
+    m = synth.make_mechanism("usc111")
+    h = pj.pj_mech_create(m)
+    n = 262144
+    phi_h, par_h = synth.make_states(m, n, 2018 + 3, synth.CONP)
+    phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+    hs = torch.from_numpy(synth.make_step_sizes(n, 2018 + 3)).to(dev)
+    f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    wb = h.workspace_size(pj.PJ_OP_NEWTON, n)
+    w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    M = torch.empty((h.nnz, n), dtype=torch.float32, device=dev)
+    t = _time(torch, stream, lambda: pj.pj_newton_matrix_f32(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, hs, 1.0, M, f,
+                                                             None, w, wb, stream), reps=3)
+    out["usc111_256k_newton_f32_csr"] = n / (t * 1e-3)
+    del M
+    J = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    t = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f, None,
+                                                                w, wb, stream), reps=3)
+    out["usc111_256k_jacobian_f64_csr"] = n / (t * 1e-3)
+    del J, w
+    # 53 species / 325 reactions, 65,536 states: adjoint VJP
+    m = synth.make_mechanism("gri53")
+    h = pj.pj_mech_create(m)
+    n = 65536
+    phi_h, par_h = synth.make_states(m, n, 2018 + 4, synth.CONP)
+    phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+    uw_h, uT_h = synth.make_cotangents(m.n_species, n, 2018 + 4)
+    uw, uT = torch.from_numpy(uw_h).to(dev), torch.from_numpy(uT_h).to(dev)
+    y = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    g = torch.empty_like(y)
+    gt = torch.empty((m.n_reactions, 3), dtype=torch.float64, device=dev)
+    wb = h.workspace_size(pj.PJ_OP_VJP, n)
+    w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    t = _time(torch, stream, lambda: pj.pj_vjp(h, synth.CONP, n, par, phi, n, uw, uT, y, g, gt, None, w, wb, stream),
+              reps=10)
+    out["gri53_64k_vjp"] = n / (t * 1e-3)
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
     import synth
     if rank != 0:
@@ -169,11 +236,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1048576, help="states per GPU")
+    ap.add_argument("--n", type=int, default=None, help="states per GPU (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--op", default="jac_csr", choices=["jac_csr", "jac_csc", "jac_dense", "source"],
+    ap.add_argument("--op", default="jac_csr",
+                    choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp"],
                     help="what one step evaluates (default: source terms + CSR Jacobian)")
     ap.add_argument("--mode", default="conp", choices=["conp", "conv"])
     args = ap.parse_args()
@@ -194,16 +262,27 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     pj.load_library()
-    m = synth.make_mechanism("gri53")
+    mech_name = {"newton": "usc111"}.get(args.op, "gri53")
+    default_n = {"newton": 262144, "vjp": 65536}.get(args.op, 1048576)
+    m = synth.make_mechanism(mech_name)
     h = pj.pj_mech_create(m)
-    n = args.n
+    n = args.n or default_n
     mode = synth.CONP if args.mode == "conp" else synth.CONV
     phi_h, par_h = synth.make_states(m, n, 2018 + 2 + 1000 * rank, mode)
     dev = torch.device("cuda", local)
     phi = torch.from_numpy(phi_h).to(dev)
     par = torch.from_numpy(par_h).to(dev)
     N1 = m.n_species + 1
-    vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
+    if args.op == "newton":
+        vals = torch.empty((h.nnz, n), dtype=torch.float32, device=dev)
+        hstep = torch.from_numpy(synth.make_step_sizes(n, 2018 + 3)).to(dev)
+    elif args.op == "vjp":
+        uw_h, uT_h = synth.make_cotangents(m.n_species, n, 2018 + 4)
+        u_w, u_T = torch.from_numpy(uw_h).to(dev), torch.from_numpy(uT_h).to(dev)
+        vals = torch.empty((N1, n), dtype=torch.float64, device=dev)          # g_phi
+        g_th = torch.empty((m.n_reactions, 3), dtype=torch.float64, device=dev)
+    else:
+        vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
     dphi = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -211,10 +290,18 @@ def main():
     work = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
     wbs = h.workspace_size(pj.PJ_OP_SOURCE, n)
     work_s = torch.empty(max(wbs, 1), dtype=torch.uint8, device=dev)
+    if args.op == "vjp":
+        wb = h.workspace_size(pj.PJ_OP_VJP, n)
+        work = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
 
     def step():
         if args.op == "source":
             pj.pj_eval_source_terms(h, mode, n, par, phi, n, dphi, status, work_s, wbs, stream)
+        elif args.op == "newton":
+            pj.pj_newton_matrix_f32(h, mode, pj.PJ_CSR, n, par, phi, n, hstep, 1.0, vals, dphi, status, work, wb,
+                                    stream)
+        elif args.op == "vjp":
+            pj.pj_vjp(h, mode, n, par, phi, n, u_w, u_T, dphi, vals, g_th, status, work, wb, stream)
         elif args.op == "jac_dense":
             pj.pj_eval_jacobian_dense(h, mode, n, par, phi, n, vals, dphi, status, work, wb, stream)
         else:
@@ -248,14 +335,15 @@ def main():
     assert int(status.item()) == 0, "invalid states in the benchmark batch"
 
     # roofline of the (single) kernel of the step: FP64 pipe
-    fp64_work = fp64_work_per_state(m, jacobian=args.op != "source")
+    fp64_work = fp64_work_per_state(m, jacobian=args.op not in ("source",))
     achieved = fp64_work * n / (ms * 1e-3) / 1e9     # G DFMA-equivalent / s
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_source_terms" if args.op == "source" else "k_jacobian", "work_per_state": fp64_work,
+                "kernel": {"source": "k_source_terms", "vjp": "k_vjp"}.get(args.op, "k_jacobian"),
+                "work_per_state": fp64_work,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
 
     variants = {}
@@ -286,7 +374,19 @@ def main():
         del jd
         torch.cuda.empty_cache()
         N1 = m.n_species + 1
-    vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
+    if args.op == "newton":
+        vals = torch.empty((h.nnz, n), dtype=torch.float32, device=dev)
+        hstep = torch.from_numpy(synth.make_step_sizes(n, 2018 + 3)).to(dev)
+    elif args.op == "vjp":
+        uw_h, uT_h = synth.make_cotangents(m.n_species, n, 2018 + 4)
+        u_w, u_T = torch.from_numpy(uw_h).to(dev), torch.from_numpy(uT_h).to(dev)
+        vals = torch.empty((N1, n), dtype=torch.float64, device=dev)          # g_phi
+        g_th = torch.empty((m.n_reactions, 3), dtype=torch.float64, device=dev)
+    else:
+        vals = torch.empty((N1 * N1 if args.op == "jac_dense" else h.nnz, n), dtype=torch.float64, device=dev)
+
+    if not args.no_variants and args.op == "jac_csr":
+        variants.update(other_workloads(pj, synth, torch, dev, stream))
 
     e2e = None
     if not args.no_e2e and args.op == "jac_csr":
@@ -330,9 +430,13 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mechanism": "synthetic 53 species / 325 reactions (seed 1811)",
+            "config": {"workload": {"newton": "usc111_256k", "vjp": "gri53_vjp64k"}.get(args.op, WORKLOAD),
+                   "mechanism": "synthetic %d species / %d reactions (seed %d)" % (
+                       m.n_species, m.n_reactions, synth.SPECS[mech_name].seed),
                        "states_per_gpu": n, "mode": args.mode.upper(), "op": args.op,
-                       "output": {"jac_csr": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
+                       "output": {"newton": "FP32 Newton matrix I - h J (CSR, nnz %d) + FP64 source terms" % h.nnz,
+                                  "vjp": "y = (wdot, dT/dt), g_phi and summed g_theta",
+                                  "jac_csr": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
                                   "jac_csc": "source terms + CSC Jacobian (nnz %d)" % h.nnz,
                                   "jac_dense": "source terms + dense Jacobian (%d entries)" % (N1 * N1),
                                   "source": "source terms"}[args.op],

@@ -181,6 +181,20 @@ int pj_eval_jacobian_dense(const pj_mech* mech, int mode, int64_t n, const doubl
                            const double* d_phi, int64_t ld, double* d_jac, double* d_dphi,
                            int* d_status, void* d_work, size_t work_bytes, void* stream);
 
+/* Newton-iteration matrix M = I - h*gamma*J in FP32 (the matrix an implicit
+ * integrator factors; the paper motivates the Jacobian by implicit
+ * integration, Sec. 1, Sec. 3.3).  Rates, Gibbs-energy differences and
+ * equilibrium constants, every exponential and the source terms are FP64;
+ * the derivative arithmetic, the accumulation of J and the assembly of M are
+ * FP32.  d_h[n] is the per-state step h (device), gamma a scalar; fmt is
+ * PJ_CSR / PJ_CSC (values in pj_sparsity order, the diagonal is in the
+ * pattern) or PJ_DENSE; d_M[e*ld + s] is float.  d_dphi (required) receives
+ * the FP64 source terms.  Workspace as for pj_eval_jacobian_sparse
+ * (PJ_OP_NEWTON). */
+int pj_newton_matrix_f32(const pj_mech* mech, int mode, int fmt, int64_t n, const double* d_param,
+                         const double* d_phi, int64_t ld, const double* d_h, double gamma, float* d_M,
+                         double* d_dphi, int* d_status, void* d_work, size_t work_bytes, void* stream);
+
 /* Allocation-free variant of pj_eval_jacobian_sparse (no counterpart in the
  * paper).  For callers that cannot allocate device memory or call an
  * allocating library routine, and so cannot supply d_work: the per-state
@@ -205,10 +219,31 @@ int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int6
 #define PJ_OP_JACOBIAN 1
 #define PJ_OP_NEWTON 2
 #define PJ_OP_VJP 3
+#define PJ_OP_Y 4
 
 /* Device scratch (bytes) an operation needs for a batch of n states; 0 when
- * the per-state working arrays fit in shared memory. */
+ * the per-state working arrays fit in shared memory (PJ_OP_VJP always needs
+ * room for its per-warp parameter-gradient partial sums). */
 int pj_workspace_size(const pj_mech* mech, int op, int64_t n, size_t* bytes);
+
+/* Forward values of the differentiation form: y = (wdot_0 .. wdot_{Ns-1},
+ * dT/dt) per state, the species production rates of Sec. 2.2 (bath gas
+ * included) and the temperature source term; d_y[k*ld + s], k in [0, Ns].
+ * Workspace: pj_workspace_size(PJ_OP_Y). */
+int pj_eval_y(const pj_mech* mech, int mode, int64_t n, const double* d_param, const double* d_phi,
+              int64_t ld, double* d_y, int* d_status, void* d_work, size_t work_bytes, void* stream);
+
+/* Vector-Jacobian product of y (see pj_eval_y) for sensitivity analysis:
+ * with cotangents d_u_wdot[k*ld + s] (k < Ns) and d_u_T[s],
+ *   d_g_phi[j*ld + s] = sum_y u_y dy/dPhi_j        (per state, j in [0, Ns])
+ *   d_g_theta[3*i + p] = sum_s sum_y u_y dy/dtheta_ip  (summed over states)
+ * for the per-reaction parameters theta_i = (ln A_i, beta_i, Ea_i) of the
+ * high-pressure (or only) Arrhenius rate, reactions in description order
+ * (Ea in cal/mol).  d_y receives y.  The state sum is deterministic for a
+ * given (mechanism, n).  Workspace: pj_workspace_size(PJ_OP_VJP), required. */
+int pj_vjp(const pj_mech* mech, int mode, int64_t n, const double* d_param, const double* d_phi, int64_t ld,
+           const double* d_u_wdot, const double* d_u_T, double* d_y, double* d_g_phi, double* d_g_theta,
+           int* d_status, void* d_work, size_t work_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,52 @@ def outputs_y(mech, mode, phi, param, **over):
     return np.concatenate([r["wdot"], f[:1]], axis=0)
 
 
+def y_jacobian(mech, mode, phi, param):
+    """dy/dPhi [Ns+1, Ns+1, n] by complex-step differentiation."""
+    N = mech.n_species + 1
+    Jy = np.empty((N, N, phi.shape[1]))
+    for j in range(N):
+        ph = phi.astype(np.complex128)
+        hj = _cs_step(phi[j])
+        ph[j] = ph[j] + 1j * hj
+        Jy[:, j] = outputs_y(mech, mode, ph, param.astype(np.complex128)).imag / hj
+    return Jy
+
+
+def vjp_envelope(mech, mode, phi, param, u_wdot, u_T):
+    """Absolute envelopes of the VJP: sum of |u_y dy/dPhi_j| per state, and
+    sum over states of |w_q dq_i/dtheta| per reaction parameter."""
+    Jy = y_jacobian(mech, mode, phi, param)
+    u = np.concatenate([u_wdot, u_T[None, :]], axis=0)
+    env_phi = np.sum(np.abs(u)[:, None, :] * np.abs(Jy), axis=0)
+    return env_phi, _theta_terms(mech, mode, phi, param, u_wdot, u_T, absolute=True)
+
+
+def _theta_terms(mech, mode, phi, param, u_wdot, u_T, absolute=False):
+    r0 = rates(mech, mode, phi, param)
+    _, aux = source_terms_from_rates(mech, mode, r0)
+    nu = r0["nu"].astype(float)                                 # [Ns, Nr]
+    # dy/dq_i per state: wdot_k -> nu_ki ; dT/dt -> -sum_k E_k nu_ki / den
+    E = aux["E"]                                                # [Ns, n]
+    w_q = (nu.T @ u_wdot)                                        # [Nr, n]
+    w_q = w_q - (nu.T @ E) * (u_T / aux["den"])[None, :]
+    f = np.abs if absolute else (lambda x: x)
+    g_theta = np.zeros((mech.n_reactions, 3))
+    hA = 1e-30
+    A_c = mech.A * np.exp(1j * hA)
+    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128), A=A_c)["q"]
+    g_theta[:, 0] = np.sum(f(w_q * (q.imag / hA)), axis=1)
+    hb = 1e-30
+    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128),
+              beta=mech.beta + 1j * hb)["q"]
+    g_theta[:, 1] = np.sum(f(w_q * (q.imag / hb)), axis=1)
+    hE = _cs_step(mech.Ea)
+    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128),
+              Ea=mech.Ea + 1j * hE)["q"]
+    g_theta[:, 2] = np.sum(f(w_q * (q.imag / hE[:, None])), axis=1)
+    return g_theta
+
+
 def vjp(mech, mode, phi, param, u_wdot, u_T):
     """(g_phi [Ns+1, n], g_theta [Nr, 3]) with g_theta summed over states."""
     ns, N = mech.n_species, mech.n_species + 1
@@ -48,24 +94,4 @@ def vjp(mech, mode, phi, param, u_wdot, u_T):
     # parameter derivatives: q_i depends only on reaction i's own parameters,
     # so one complex evaluation per parameter kind gives d q_i / d theta_i for
     # every i at once; y is then linear in q.
-    r0 = rates(mech, mode, phi, param)
-    _, aux = source_terms_from_rates(mech, mode, r0)
-    nu = r0["nu"].astype(float)                                 # [Ns, Nr]
-    # dy/dq_i per state: wdot_k -> nu_ki ; dT/dt -> -sum_k E_k nu_ki / den
-    E = aux["E"]                                                # [Ns, n]
-    w_q = (nu.T @ u_wdot)                                        # [Nr, n]
-    w_q = w_q - (nu.T @ E) * (u_T / aux["den"])[None, :]
-    g_theta = np.zeros((mech.n_reactions, 3))
-    hA = 1e-30
-    A_c = mech.A * np.exp(1j * hA)
-    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128), A=A_c)["q"]
-    g_theta[:, 0] = np.sum(w_q * (q.imag / hA), axis=1)
-    hb = 1e-30
-    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128),
-              beta=mech.beta + 1j * hb)["q"]
-    g_theta[:, 1] = np.sum(w_q * (q.imag / hb), axis=1)
-    hE = _cs_step(mech.Ea)
-    q = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128),
-              Ea=mech.Ea + 1j * hE)["q"]
-    g_theta[:, 2] = np.sum(w_q * (q.imag / hE[:, None]), axis=1)
-    return g_phi, g_theta
+    return g_phi, _theta_terms(mech, mode, phi, param, u_wdot, u_T)

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native as N
 from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
-                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_MAX_SP, check)
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_MAX_SP, check)
 
 
 def _ptr(t):
@@ -142,6 +142,26 @@ def pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, jac, dphi=None, status
                  "pj_eval_jacobian_dense")
 
 
+def pj_eval_y(mech, mode, n, param, phi, ld, y, status=None, work=None, work_bytes=0, stream=None):
+    return check(N.load().pj_eval_y(mech.handle, mode, n, _ptr(param), _ptr(phi), ld, _ptr(y), _ptr(status),
+                                     _ptr(work), work_bytes, _stream(stream)), "pj_eval_y")
+
+
+def pj_vjp(mech, mode, n, param, phi, ld, u_wdot, u_T, y, g_phi, g_theta, status=None, work=None, work_bytes=0,
+           stream=None):
+    return check(N.load().pj_vjp(mech.handle, mode, n, _ptr(param), _ptr(phi), ld, _ptr(u_wdot), _ptr(u_T),
+                                  _ptr(y), _ptr(g_phi), _ptr(g_theta), _ptr(status), _ptr(work), work_bytes,
+                                  _stream(stream)), "pj_vjp")
+
+
+def pj_newton_matrix_f32(mech, mode, fmt, n, param, phi, ld, h, gamma, M, dphi, status=None, work=None,
+                         work_bytes=0, stream=None):
+    return check(N.load().pj_newton_matrix_f32(mech.handle, mode, fmt, n, _ptr(param), _ptr(phi), ld, _ptr(h),
+                                                float(gamma), _ptr(M), _ptr(dphi), _ptr(status), _ptr(work),
+                                                work_bytes, _stream(stream)),
+                 "pj_newton_matrix_f32")
+
+
 def pj_eval_jacobian_sparse_noalloc(mech, mode, fmt, n, param, phi, ld, vals, dphi, status=None, stream=None):
     """Sparse Jacobian without a workspace argument, for callers that cannot
     allocate device memory: the library's fixed per-device scratch array is
@@ -211,3 +231,92 @@ def jacobian_dense(mech, mode, phi, param, out=None, dphi=None, status=None, str
     work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
     pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, out, dphi, status, work, wb, stream)
     return out
+
+
+def newton_matrix_f32(mech, mode, phi, param, h, gamma=1.0, fmt=PJ_CSR, out=None, dphi=None, status=None,
+                      stream=None):
+    """FP32 M = I - h*gamma*J (CSR/CSC values or dense rows) and FP64 source terms."""
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    N1 = mech.n_species + 1
+    rows = N1 * N1 if fmt == PJ_DENSE else mech.nnz
+    if out is None:
+        out = torch.empty((rows, ld), dtype=torch.float32, device=phi.device)[:, :n]
+    if dphi is None:
+        dphi = _dphi_like(mech, phi, ld, n)
+    work, wb = _workspace(mech, PJ_OP_NEWTON, n, phi.device)
+    pj_newton_matrix_f32(mech, mode, fmt, n, param, phi, ld, h, gamma, out, dphi, status, work, wb, stream)
+    return out
+
+
+def eval_y(mech, mode, phi, param, out=None, status=None, stream=None):
+    """y = (wdot_0 .. wdot_{Ns-1}, dT/dt), shape [Ns+1, n]."""
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    if out is None:
+        out = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    work, wb = _workspace(mech, PJ_OP_Y, n, phi.device)
+    pj_eval_y(mech, mode, n, param, phi, ld, out, status, work, wb, stream)
+    return out
+
+
+def vjp(mech, mode, phi, param, u_wdot, u_T, status=None, stream=None):
+    """(y, g_phi [Ns+1, n], g_theta [Nr, 3]) for cotangents u_wdot [Ns, n], u_T [n]."""
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    if u_wdot.shape != (mech.n_species, n) or u_wdot.stride() != (ld, 1) or u_T.shape != (n,):
+        raise ValueError("u_wdot must be [Ns, n] with the leading dimension of phi, u_T [n]")
+    y = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    g_phi = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    g_theta = torch.empty((mech.n_reactions, 3), dtype=torch.float64, device=phi.device)
+    work, wb = _workspace(mech, PJ_OP_VJP, n, phi.device)
+    pj_vjp(mech, mode, n, param, phi, ld, u_wdot, u_T.contiguous(), y, g_phi, g_theta, status, work, wb, stream)
+    return y, g_phi, g_theta
+
+
+def arrhenius_parameters(mech_data):
+    """theta [Nr, 3] = (ln A, beta, Ea) of the high-pressure (or only) rate of a
+    mechanism description, as a float64 CPU tensor."""
+    import torch
+    return torch.tensor(np.stack([np.log(np.asarray(mech_data.A, float)), np.asarray(mech_data.beta, float),
+                                  np.asarray(mech_data.Ea, float)], axis=1))
+
+
+def _make_function():
+    import torch
+
+    class SourceTermsY(torch.autograd.Function):
+        """y(phi, theta) = (wdot_0 .. wdot_{Ns-1}, dT/dt) with gradients by the
+        adjoint kernel.  theta [Nr, 3] must hold the mechanism's (ln A, beta,
+        Ea); it is the graph node for parameter sensitivities (the kernels
+        read the values packed in the mechanism)."""
+
+        @staticmethod
+        def forward(ctx, phi, theta, mech, mode, param):
+            ctx.mech, ctx.mode = mech, mode
+            ctx.save_for_backward(phi, param)
+            return eval_y(mech, mode, phi.detach(), param)
+
+        @staticmethod
+        def backward(ctx, gy):
+            phi, param = ctx.saved_tensors
+            ns = ctx.mech.n_species
+            gy = gy.contiguous()
+            n = phi.shape[1]
+            u_wdot = torch.empty((ns, max(phi.stride(0), 1)), dtype=torch.float64, device=phi.device)[:, :n]
+            u_wdot.copy_(gy[:ns])
+            _, g_phi, g_theta = vjp(ctx.mech, ctx.mode, phi.detach(), param, u_wdot, gy[ns])
+            return g_phi, g_theta.to(phi.device), None, None, None
+
+    return SourceTermsY
+
+
+_Y = None
+
+
+def source_terms_y(mech, mode, phi, param, theta):
+    """Differentiable y = (wdot, dT/dt) (torch.autograd.Function)."""
+    global _Y
+    if _Y is None:
+        _Y = _make_function()
+    return _Y.apply(phi, theta, mech, mode, param)

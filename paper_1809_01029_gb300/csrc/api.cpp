@@ -13,6 +13,15 @@ int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double
                     int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
                     cudaStream_t st);
 size_t workspace_bytes(int arrays, int ns, int64_t n);
+size_t form_workspace_bytes(int op, const DevMech& m, int64_t n);
+int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
+                  double* y, int* status, void* work, size_t work_bytes, cudaStream_t st);
+int launch_vjp(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
+               const double* u_wdot, const double* u_T, double* y, double* g_phi, double* g_theta, int* status,
+               void* work, size_t work_bytes, cudaStream_t st);
+int launch_newton_f32(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
+                      int64_t ld, const double* hstep, double gamma, float* M, double* dphi, int* status,
+                      void* work, size_t work_bytes, cudaStream_t st);
 int source_arrays();
 int jacobian_arrays();
 
@@ -44,6 +53,8 @@ extern "C" int pj_workspace_size(const pj_mech* m, int op, int64_t n, size_t* by
     case PJ_OP_SOURCE: *bytes = workspace_bytes(source_arrays(), m->ns, n); return PJ_OK;
     case PJ_OP_JACOBIAN:
     case PJ_OP_NEWTON: *bytes = workspace_bytes(jacobian_arrays(), m->ns, n); return PJ_OK;
+    case PJ_OP_VJP:
+    case PJ_OP_Y: *bytes = form_workspace_bytes(op, m->dm, n); return PJ_OK;
     default: return fail(PJ_ERR_ARG, "pj_workspace_size: unknown op");
   }
 }
@@ -78,4 +89,39 @@ extern "C" int pj_eval_jacobian_dense(const pj_mech* m, int mode, int64_t n, con
   if (n == 0) return PJ_OK;
   return launch_jacobian(m->dm, mode, PJ_DENSE, n, param, phi, ld, jac, dphi, status, work, work_bytes,
                          (cudaStream_t)stream);
+}
+
+extern "C" int pj_newton_matrix_f32(const pj_mech* m, int mode, int fmt, int64_t n, const double* param,
+                                    const double* phi, int64_t ld, const double* h, double gamma, float* M,
+                                    double* dphi, int* status, void* work, size_t work_bytes, void* stream) {
+  if (fmt != PJ_CSR && fmt != PJ_CSC && fmt != PJ_DENSE)
+    return fail(PJ_ERR_ARG, "pj_newton_matrix_f32: fmt must be PJ_CSR, PJ_CSC or PJ_DENSE");
+  int rc = check_common("pj_newton_matrix_f32", m, mode, n, ld, param, phi, M);
+  if (rc) return rc;
+  if (n > 0 && (!dphi || !h)) return fail(PJ_ERR_ARG, "pj_newton_matrix_f32: d_h and d_dphi are required");
+  if (!(gamma == gamma)) return fail(PJ_ERR_ARG, "pj_newton_matrix_f32: gamma is NaN");
+  if (n == 0) return PJ_OK;
+  return launch_newton_f32(m->dm, mode, fmt, n, param, phi, ld, h, gamma, M, dphi, status, work, work_bytes,
+                           (cudaStream_t)stream);
+}
+
+extern "C" int pj_eval_y(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
+                         double* y, int* status, void* work, size_t work_bytes, void* stream) {
+  int rc = check_common("pj_eval_y", m, mode, n, ld, param, phi, y);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_eval_y(m->dm, mode, n, param, phi, ld, y, status, work, work_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int pj_vjp(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
+                      const double* u_wdot, const double* u_T, double* y, double* g_phi, double* g_theta,
+                      int* status, void* work, size_t work_bytes, void* stream) {
+  int rc = check_common("pj_vjp", m, mode, n, ld, param, phi, g_phi);
+  if (rc) return rc;
+  if (n > 0 && (!u_wdot || !u_T || !y)) return fail(PJ_ERR_ARG, "pj_vjp: d_u_wdot, d_u_T and d_y are required");
+  if (!g_theta) return fail(PJ_ERR_ARG, "pj_vjp: d_g_theta is required");
+  if (n == 0) return cudaMemsetAsync(g_theta, 0, sizeof(double) * 3 * (size_t)m->nr, (cudaStream_t)stream) == cudaSuccess
+                         ? PJ_OK : fail(PJ_ERR_CUDA, "pj_vjp: cudaMemsetAsync failed");
+  return launch_vjp(m->dm, mode, n, param, phi, ld, u_wdot, u_T, y, g_phi, g_theta, status, work, work_bytes,
+                    (cudaStream_t)stream);
 }

@@ -23,226 +23,9 @@
 //    load (the mapping Sec. 3.3 proposes instead of a per-entry search).
 #include <cuda_runtime.h>
 
-#include "kinetics_device.cuh"
-
-#ifndef PJ_DYN_SMEM
-#define PJ_DYN_SMEM extern __shared__ double smem[]
-#endif
+#include "kinetics_common.cuh"
 
 namespace pj {
-
-struct StateScalars {
-  double T, V, P, invT, lnT, Ctot;
-};
-
-// Load one state, fill C_k (k < Ns-1 as n_k/V; the bath gas as C_tot minus
-// the others summed in species order) and check validity.
-template <int MODE>
-__device__ __forceinline__ bool load_state(const DevMech& m, const double* __restrict__ phi,
-                                           const double* __restrict__ param, int64_t ld, int64_t s,
-                                           const StateArrays& A, int aC, StateScalars& st) {
-  const int ns = m.ns;
-  const double T = phi[s], S = phi[ld + s], par = param[s];
-  const double V = MODE == PJ_CONP ? S : par;
-  const double P = MODE == PJ_CONP ? par : S;
-  bool ok = (T > 0.0) && (V > 0.0) && (P > 0.0) && isfinite(T) && isfinite(V) && isfinite(P);
-  double acc = 0.0;
-  for (int k = 0; k < ns - 1; k++) {
-    const double c = phi[(int64_t)(k + 2) * ld + s] / V;
-    A.at(aC, k) = c;
-    acc += c;
-  }
-  const double Ctot = P / (RU * T);
-  const double Cns = Ctot - acc;
-  A.at(aC, ns - 1) = Cns;
-  ok = ok && isfinite(acc) && isfinite(Cns) && !(Cns < -1e-12 * Ctot);
-  st.T = T;
-  st.V = V;
-  st.P = P;
-  st.invT = 1.0 / T;
-  st.lnT = log(T);
-  st.Ctot = Ctot;
-  return ok;
-}
-
-// Troe / SRI broadening factor F(T, Pr).  With derivatives also returns
-// FxPr = Pr dF/dPr (at fixed T) and FT = dF/dT (at fixed Pr).
-template <bool DERIV>
-__device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind, double T, double invT,
-                                            double lnT, double Pr, double& FxPr, double& FT) {
-  FxPr = 0.0;
-  FT = 0.0;
-  if (kind == PJ_TROE) {
-    const double a = __ldg(&r->fp[0]), iT3 = __ldg(&r->fp[1]), iT1 = __ldg(&r->fp[2]);
-    const double T2 = __ldg(&r->fp[3]), has2 = __ldg(&r->fp[4]);
-    const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
-    const double e2 = has2 != 0.0 ? exp(-T2 * invT) : 0.0;
-    const double Fcent = (1.0 - a) * e3 + a * e1 + e2;
-    const double L = log10(Fcent);
-    const double x = log10(Pr);
-    const double cc = -0.4 - 0.67 * L;
-    const double NN = 0.75 - 1.27 * L;
-    const double xc = x + cc;
-    const double D = NN - 0.14 * xc;
-    const double f1 = xc / D;
-    const double g = 1.0 / (1.0 + f1 * f1);
-    const double F = exp(LN10 * (L * g));
-    if (DERIV) {
-      const double iD2 = 1.0 / (D * D);
-      const double m2fg2 = -2.0 * f1 * g * g;
-      const double dlg_dx = L * m2fg2 * NN * iD2;
-      const double dlg_dL = g + L * m2fg2 * (-0.67 * D + 1.1762 * xc) * iD2;
-      const double dFcent = -(1.0 - a) * iT3 * e3 - a * iT1 * e1 + T2 * invT * invT * e2;
-      FxPr = F * dlg_dx;
-      FT = F * dlg_dL * dFcent / Fcent;
-    }
-    return F;
-  }
-  if (kind == PJ_SRI) {
-    const double a = __ldg(&r->fp[0]), b = __ldg(&r->fp[1]), ic = __ldg(&r->fp[2]);
-    const double d = __ldg(&r->fp[3]), e = __ldg(&r->fp[4]);
-    const double x = log10(Pr);
-    const double X = 1.0 / (1.0 + x * x);
-    const double eb = exp(-b * invT), ec = exp(-T * ic);
-    const double Z = a * eb + ec;
-    const double lnZ = log(Z);
-    const double F = d * exp(X * lnZ + e * lnT);
-    if (DERIV) {
-      FxPr = F * (lnZ * (-2.0 * x * X * X)) * (1.0 / LN10);
-      const double dZ = a * b * invT * invT * eb - ic * ec;
-      FT = F * (X * dZ / Z + e * invT);
-    }
-    return F;
-  }
-  return 1.0;  // Lindemann
-}
-
-__device__ __forceinline__ double dneg(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
-}
-
-// nu * x with the common nu = +-1 done as a sign flip (integer pipe)
-__device__ __forceinline__ double nu_times(int nu, double nud, double x) {
-  if (nu == 1) return x;
-  if (nu == -1) return dneg(x);
-  return nud * x;
-}
-
-// R = k * prod_a C_a^nu_a over one reaction side (positions off .. off+n-1)
-// and, with DER, dR[a] = dR/dC_a.  The shape code selects the minimal
-// multiply sequence; SH_GEN falls back to a general product.
-template <bool DER>
-__device__ __forceinline__ double side_rate(const StateArrays& A, int aC, const Rxn* __restrict__ r, int off,
-                                            int shape, int n, double k, double (&dR)[PJ_MAX_SP]) {
-  switch (shape) {
-    case SH_1: {
-      const double c0 = A.at(aC, __ldg(&r->sp[off]));
-      if (DER) dR[0] = k;
-      return k * c0;
-    }
-    case SH_2: {
-      const double c0 = A.at(aC, __ldg(&r->sp[off]));
-      const double t = k * c0;
-      if (DER) dR[0] = t + t;
-      return t * c0;
-    }
-    case SH_11: {
-      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
-      const double t = k * c1;
-      if (DER) {
-        dR[0] = t;
-        dR[1] = k * c0;
-      }
-      return t * c0;
-    }
-    case SH_21: {
-      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
-      const double t = k * c0;
-      const double t1 = t * c1;
-      if (DER) {
-        dR[0] = t1 + t1;
-        dR[1] = t * c0;
-      }
-      return t1 * c0;
-    }
-    case SH_111: {
-      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
-      const double c2 = A.at(aC, __ldg(&r->sp[off + 2]));
-      const double t2 = k * c2;
-      const double t12 = t2 * c1;
-      if (DER) {
-        dR[0] = t12;
-        dR[1] = t2 * c0;
-        dR[2] = (k * c0) * c1;
-      }
-      return t12 * c0;
-    }
-    default: {
-      double pw[PJ_MAX_SP], dpw[PJ_MAX_SP];
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++) {
-        pw[a] = 1.0;
-        dpw[a] = 0.0;
-        if (a < n) {
-          const int v = __ldg(&r->nu[off + a]);
-          const double c = A.at(aC, __ldg(&r->sp[off + a]));
-          const double cm = powi(c, v - 1);
-          pw[a] = cm * c;
-          dpw[a] = v * cm;
-        }
-      }
-      double R = k;
-#pragma unroll
-      for (int a = 0; a < PJ_MAX_SP; a++)
-        if (a < n) R *= pw[a];
-      if (DER) {
-#pragma unroll
-        for (int a = 0; a < PJ_MAX_SP; a++) {
-          if (a >= n) continue;
-          double p = k * dpw[a];
-#pragma unroll
-          for (int b = 0; b < PJ_MAX_SP; b++)
-            if (b != a && b < n) p *= pw[b];
-          dR[a] = p;
-        }
-      }
-      return R;
-    }
-  }
-}
-
-// Forward and reverse rate constants; the two exponentials sit in one basic
-// block so their dependency chains interleave.
-__device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, const Rxn* __restrict__ r, int rev,
-                                               int nre, int npr, double lnkf, double logPRT, double& kf,
-                                               double& kr) {
-  if (rev) {
-    double dg = 0.0;
-#pragma unroll
-    for (int a = 0; a < PJ_MAX_SP; a++) {
-      if (a < nre) dg = fma(-__ldg(&r->nud[a]), A.at(aG, __ldg(&r->sp[a])), dg);
-      if (a < npr) dg = fma(__ldg(&r->nud[PJ_MAX_SP + a]), A.at(aG, __ldg(&r->sp[PJ_MAX_SP + a])), dg);
-    }
-    // kr = kf / Kc with Kc = exp(-dg) (P_std / R T)^dnu
-    const double larg = lnkf + dg - __ldg(&r->dnu) * logPRT;
-    kf = exp(lnkf);
-    kr = exp(larg);
-  } else {
-    kf = exp(lnkf);
-    kr = 0.0;
-  }
-}
-
-// Third-body concentration [M] = C_tot + sum_e (alpha_e - 1) C_e.
-__device__ __forceinline__ double third_body(const DevMech& m, const StateArrays& A, int aC, const Rxn* __restrict__ r,
-                                             double Ctot) {
-  double M = Ctot;
-  for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
-    M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
-  return M;
-}
-
-__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }  // result unused: red.global.add.f64
 
 // ---------------------------------------------------------------------------
 // source terms
@@ -361,18 +144,37 @@ __device__ __forceinline__ int64_t jpos(const DevMech& m, int row, int col) {
   return __ldg(p + (int64_t)row * m.N + col);
 }
 
-__device__ __forceinline__ void jred(double* J, int64_t e, int64_t ld, int64_t s, double v) {
+__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }  // red.global.add.f32
+
+template <typename DT>
+__device__ __forceinline__ void jred(DT* J, int64_t e, int64_t ld, int64_t s, DT v) {
   if (e >= 0) red_add(J + e * ld + s, v);
 }
 
+__device__ __forceinline__ float dneg(float x) { return -x; }
+
+template <typename DT>
+__device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
+  if (nu == 1) return x;
+  if (nu == -1) return dneg(x);
+  return DT(nud) * x;
+}
+
+// Analytical Jacobian (Sec. 2.2, Sec. 3.3).  Rates, equilibrium constants,
+// exponentials and source terms are always FP64.  DT is the type of the
+// derivative arithmetic, the entry accumulation and the output: double for
+// J itself, float for the Newton-matrix form.  With NEWTON the final pass
+// turns the accumulated J into M = I - h*gamma*J in place (h per state).
+//
 // Shared memory holds C_k, g_k/RT and h_k/RT per state.  Production rates go
 // to the source-term output by L2 reductions (bath gas in a register);
 // Jacobian entries to the zero-initialised output by L2 reductions.
-template <int MODE, int FMT>
+template <int MODE, int FMT, typename DT, bool NEWTON>
 __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const double* __restrict__ param,
                                                   const double* __restrict__ phi, int64_t ld,
-                                                  double* __restrict__ J, double* __restrict__ dphi,
-                                                  int* status, double* ws, int64_t ws_stride) {
+                                                  DT* __restrict__ J, double* __restrict__ dphi,
+                                                  int* status, double* ws, int64_t ws_stride,
+                                                  const double* __restrict__ hstep, double gamma) {
   PJ_DYN_SMEM;
   const int ns = m.ns, N = m.N, bath = m.ns - 1;
   const int64_t n_out = FMT == PJ_DENSE ? (int64_t)N * N : (int64_t)m.nnz;
@@ -390,14 +192,16 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     StateScalars st;
     if (!load_state<MODE>(m, phi, param, ld, s, A, aC, st)) {
-      write_nan_state(J, ld, s, (int)n_out);
+      const DT qnan = DT(__longlong_as_double(0x7ff8000000000000ULL));
+      for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = qnan;
       write_nan_state(dphi, ld, s, ns + 1);
       if (status) atomicAdd(status, 1);
       continue;
     }
     const double T = st.T, V = st.V, P = st.P, invT = st.invT, lnT = st.lnT, Ctot = st.Ctot;
     const double invT2 = invT * invT, invV = 1.0 / V;
-    for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = 0.0;
+    const DT invT_t = DT(invT), invT2_t = DT(invT2), invV_t = DT(invV), V_t = DT(V);
+    for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = DT(0);
     double* __restrict__ wrow = dphi + 2 * ld + s;  // wdot_k accumulates at wrow[k*ld]
     for (int k = 0; k < ns - 1; k++) wrow[(int64_t)k * ld] = 0.0;
 
@@ -421,13 +225,15 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     // derivatives of the bath-gas concentration
     const double dCb_T = -Ctot * invT;
     const double dCb_S = MODE == PJ_CONP ? (Ctot - C_bath) * invV : Ctot / P;
+    const DT dCb_T_t = DT(dCb_T), dCb_S_t = DT(dCb_S);
     dden_T = RU * dden_T + Cx_bath * dCb_T;
     const double dden_S = MODE == PJ_CONP ? (Cx_bath * Ctot - den) * invV : Cx_bath * Ctot / P;
     const double logPRT = m.log_pstd_over_r - lnT;
 
     // accumulators of the energy row (T) and state row (S) for the T and S
     // columns and for the part common to every species column
-    double AT_T = 0, AT_S = 0, AS_T = 0, AS_S = 0, ATB = 0, ASB = 0, w_bath = 0;
+    DT AT_T = 0, AT_S = 0, AS_T = 0, AS_S = 0, ATB = 0, ASB = 0;
+    double w_bath = 0;
 
     for (int i = 0; i < m.nr; i++) {
       const Rxn* __restrict__ r = m.rxn + i;
@@ -436,7 +242,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       const int rev = __ldg(&r->rev);
       const double beta = __ldg(&r->beta), theta = __ldg(&r->theta);
       const double lnkf = fma(beta, lnT, __ldg(&r->lnA)) - theta * invT;
-      const double dlnkf = fma(theta, invT2, beta * invT);
+      const DT dlnkf = DT(theta) * invT2_t + DT(beta) * invT_t;
       double kf, kr;
       rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
       double dh = 0.0;
@@ -447,72 +253,83 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       }
       double dRf[PJ_MAX_SP], dRr[PJ_MAX_SP];
       const double Rf = side_rate<true>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dRf);
-      double Rr = 0.0, dlnkr = 0.0;
+      double Rr = 0.0;
+      DT dlnkr = DT(0);
       if (rev) {
         Rr = side_rate<true>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dRr);
-        dlnkr = dlnkf - (dh - __ldg(&r->dnu)) * invT;
+        dlnkr = dlnkf - DT(dh - __ldg(&r->dnu)) * invT_t;
       }
       const double Rn = Rf - Rr;
+      const DT Rn_t = DT(Rn);
 
-      // pressure modification c and its derivatives
-      double c = 1.0, dcdT = 0.0, dcdS = 0.0, dcdM = 0.0;
+      // pressure modification c (FP64) and its derivatives (DT)
+      double c = 1.0;
+      DT dcdT = 0, dcdS = 0, dcdM = 0;
       if (kind != PJ_ELEMENTARY) {
         const double M = third_body(m, A, aC, r, Ctot);
-        const double ab = __ldg(&r->alpha_bath);
-        const double dMdT = ab * dCb_T;
-        const double dMdS = MODE == PJ_CONP ? (ab * Ctot - M) * invV : ab * Ctot / P;
+        const DT ab = DT(__ldg(&r->alpha_bath));
+        const DT dMdT = ab * dCb_T_t;
+        const DT dMdS = MODE == PJ_CONP ? (ab * DT(Ctot) - DT(M)) * invV_t : ab * DT(Ctot / P);
         if (kind == PJ_THIRD_BODY) {
           c = M;
-          dcdM = 1.0;
+          dcdM = DT(1);
           dcdT = dMdT;
           dcdS = dMdS;
         } else {
           const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
           const double lnk0 = fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
-          const double dlnk0 = fma(theta0, invT2, beta0 * invT);
+          const DT dlnk0 = DT(theta0) * invT2_t + DT(beta0) * invT_t;
           const double rk = exp(lnk0 - lnkf);
           const double Pr = rk * M;
-          double FxPr, FT;
-          const double F = falloff_F<true>(r, kind, T, invT, lnT, Pr, FxPr, FT);
+          DT FxPr, FT;
+          const double F = falloff_F<true, DT>(r, kind, T, invT, lnT, Pr, FxPr, FT);
           const double i1p = 1.0 / (1.0 + Pr);
           const double fr = Pr * i1p;
           c = fr * F;
-          const double cPr = F * i1p * i1p + FxPr * i1p;
-          const double dPrdT = Pr * (dlnk0 - dlnkf) + rk * dMdT;
-          dcdT = fr * FT + cPr * dPrdT;
-          dcdM = cPr * rk;
+          const DT i1p_t = DT(i1p), F_t = DT(F), Pr_t = DT(Pr), rk_t = DT(rk);
+          const DT cPr = F_t * i1p_t * i1p_t + FxPr * i1p_t;
+          const DT dPrdT = Pr_t * (dlnk0 - dlnkf) + rk_t * dMdT;
+          dcdT = DT(fr) * FT + cPr * dPrdT;
+          dcdM = cPr * rk_t;
           dcdS = dcdM * dMdS;
         }
+      }
+      const DT c_t = DT(c);
+      DT dRf_t[PJ_MAX_SP], dRr_t[PJ_MAX_SP];
+#pragma unroll
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        dRf_t[a] = a < nre ? DT(dRf[a]) : DT(0);
+        dRr_t[a] = (rev && a < npr) ? DT(dRr[a]) : DT(0);
       }
 
       // derivatives of the net rate in T and S (rate constants, and the bath
       // gas through C_Ns = C_tot - sum C_k)
-      double dRdT = Rf * dlnkf - Rr * dlnkr;
-      double dRdS = 0.0;
+      DT dRdT = DT(Rf) * dlnkf - DT(Rr) * dlnkr;
+      DT dRdS = DT(0);
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
         if (a < nre) {
           const int k = __ldg(&r->sp[a]);
           if (k == bath) {
-            dRdT = fma(dRf[a], dCb_T, dRdT);
-            dRdS = fma(dRf[a], dCb_S, dRdS);
+            dRdT = dRdT + dRf_t[a] * dCb_T_t;
+            dRdS = dRdS + dRf_t[a] * dCb_S_t;
           } else if (MODE == PJ_CONP) {
-            dRdS = fma(dRf[a], -A.at(aC, k) * invV, dRdS);
+            dRdS = dRdS - dRf_t[a] * (DT(A.at(aC, k)) * invV_t);
           }
         }
         if (rev && a < npr) {
           const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
           if (k == bath) {
-            dRdT = fma(-dRr[a], dCb_T, dRdT);
-            dRdS = fma(-dRr[a], dCb_S, dRdS);
+            dRdT = dRdT - dRr_t[a] * dCb_T_t;
+            dRdS = dRdS - dRr_t[a] * dCb_S_t;
           } else if (MODE == PJ_CONP) {
-            dRdS = fma(dRr[a], A.at(aC, k) * invV, dRdS);
+            dRdS = dRdS + dRr_t[a] * (DT(A.at(aC, k)) * invV_t);
           }
         }
       }
       const double q = c * Rn;
-      const double dqdT = fma(c, dRdT, Rn * dcdT);
-      const double dqdS = fma(c, dRdS, Rn * dcdS);
+      const DT dqdT = c_t * dRdT + Rn_t * dcdT;
+      const DT dqdS = c_t * dRdS + Rn_t * dcdS;
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
         if (a < nre) {
@@ -530,53 +347,53 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       }
 
       // energy-row and state-row weights of this reaction
-      const double dE = RU * T * (MODE == PJ_CONP ? dh : dh - __ldg(&r->dnu));
-      const double dW = __ldg(&r->dW);
-      AT_T = fma(dE, dqdT, AT_T);
-      AT_S = fma(dE, dqdS, AT_S);
-      AS_T = fma(dW, dqdT, AS_T);
-      AS_S = fma(dW, dqdS, AS_S);
+      const DT dE = DT(RU * T * (MODE == PJ_CONP ? dh : dh - __ldg(&r->dnu)));
+      const DT dW = DT(__ldg(&r->dW));
+      AT_T = AT_T + dE * dqdT;
+      AT_S = AT_S + dE * dqdS;
+      AS_T = AS_T + dW * dqdT;
+      AS_S = AS_S + dW * dqdS;
 
       const int row_lo = __ldg(&r->row_lo), row_hi = __ldg(&r->row_hi);
-      const double VdqdT = V * dqdT, VdqdS = V * dqdS;
+      const DT VdqdT = V_t * dqdT, VdqdS = V_t * dqdS;
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
-        jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times(rn.nu, rn.nud, VdqdT));
-        jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times(rn.nu, rn.nud, VdqdS));
+        jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdT));
+        jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
       }
 
       // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i
-      double Bi = 0.0;
-      auto slot = [&](int j, double val) {
+      DT Bi = DT(0);
+      auto slot = [&](int j, DT val) {
         if (j == bath) {
-          Bi -= val;
+          Bi = Bi - val;
           return;
         }
         for (int q2 = row_lo; q2 < row_hi; q2++) {
           const RowNu rn = m.rows[q2];
-          jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times(rn.nu, rn.nud, val));
+          jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times_t<DT>(rn.nu, rn.nud, val));
         }
         jred(J, jpos<FMT>(m, 0, j + 2), ld, s, dE * val);
         jred(J, jpos<FMT>(m, 1, j + 2), ld, s, dW * val);
       };
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
-        if (a < nre) slot(__ldg(&r->sp[a]), c * dRf[a]);
-        if (rev && a < npr) slot(__ldg(&r->sp[PJ_MAX_SP + a]), dneg(c * dRr[a]));
+        if (a < nre) slot(__ldg(&r->sp[a]), c_t * dRf_t[a]);
+        if (rev && a < npr) slot(__ldg(&r->sp[PJ_MAX_SP + a]), dneg(c_t * dRr_t[a]));
       }
       if (kind != PJ_ELEMENTARY) {
-        const double t = Rn * dcdM;
+        const DT t = Rn_t * dcdM;
         for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
-          slot(__ldg(m.eff_sp + e), t * __ldg(m.eff_am1 + e));
+          slot(__ldg(m.eff_sp + e), t * DT(__ldg(m.eff_am1 + e)));
       }
       if (__ldg(&r->dense)) {
         for (int q2 = row_lo; q2 < row_hi; q2++) {
           const RowNu rn = m.rows[q2];
-          const double v = nu_times(rn.nu, rn.nud, Bi);
+          const DT v = nu_times_t<DT>(rn.nu, rn.nud, Bi);
           for (int j = 0; j < ns - 1; j++) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
         }
-        ATB = fma(dE, Bi, ATB);
-        ASB = fma(dW, Bi, ASB);
+        ATB = ATB + dE * Bi;
+        ASB = ASB + dW * Bi;
       }
     }
 
@@ -593,7 +410,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
       if (k < bath) {
         Om = fma(__ldg(m.wfac + k), wk, Om);
         wrow[(int64_t)k * ld] = V * wk;
-        if (MODE == PJ_CONP) jred(J, jpos<FMT>(m, k + 2, 1), ld, s, wk);
+        if (MODE == PJ_CONP) jred(J, jpos<FMT>(m, k + 2, 1), ld, s, DT(wk));
       }
     }
     num *= RU * T;
@@ -603,36 +420,50 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     dphi[ld + s] = Sdot;
 
     // energy row 0 and state row 1
-    const double iden = 1.0 / den;
-    const double Cx_b = A.at(aG, bath);
-    const double rtvp = MODE == PJ_CONP ? RU * T * V / P : RU * T;
+    const DT iden = DT(1.0 / den);
+    const DT Tdot_t = DT(Tdot), Om_t = DT(Om);
+    const DT Cx_b = DT(A.at(aG, bath));
+    const DT rtvp = DT(MODE == PJ_CONP ? RU * T * V / P : RU * T);
     for (int j = 0; j < N; j++) {
       const int64_t e0 = jpos<FMT>(m, 0, j), e1 = jpos<FMT>(m, 1, j);
-      double jT, dOm;
+      DT jT, dOm;
       if (j == 0) {
-        jT = -(AT_T + sumCxW + Tdot * dden_T) * iden;
+        jT = -(AT_T + DT(sumCxW) + Tdot_t * DT(dden_T)) * iden;
         dOm = AS_T;
       } else if (j == 1) {
-        jT = -(AT_S + Tdot * dden_S) * iden;
+        jT = -(AT_S + Tdot_t * DT(dden_S)) * iden;
         dOm = AS_S;
       } else {
-        const double accT = __ldcg(J + e0 * ld + s);
-        const double accS = __ldcg(J + e1 * ld + s);
-        jT = -(accT + ATB + Tdot * (A.at(aG, j - 2) - Cx_b)) * (invV * iden);
-        dOm = (accS + ASB) * invV;
+        const DT accT = __ldcg(J + e0 * ld + s);
+        const DT accS = __ldcg(J + e1 * ld + s);
+        jT = -(accT + ATB + Tdot_t * (DT(A.at(aG, j - 2)) - Cx_b)) * (invV_t * iden);
+        dOm = (accS + ASB) * invV_t;
       }
-      double jS;
+      DT jS;
       if (MODE == PJ_CONP) {
-        jS = (V * invT) * jT + rtvp * dOm;
-        if (j == 0) jS += -V * Tdot * invT2 + (RU * V / P) * Om;
-        if (j == 1) jS += Tdot * invT + (RU * T / P) * Om;
+        jS = DT(V * invT) * jT + rtvp * dOm;
+        if (j == 0) jS = jS + DT(-V * Tdot * invT2 + (RU * V / P) * Om);
+        if (j == 1) jS = jS + DT(Tdot * invT + (RU * T / P) * Om);
       } else {
-        jS = (P * invT) * jT + rtvp * dOm;
-        if (j == 0) jS += -P * Tdot * invT2 + RU * Om;
-        if (j == 1) jS += Tdot * invT;
+        jS = DT(P * invT) * jT + rtvp * dOm;
+        if (j == 0) jS = jS + DT(-P * Tdot * invT2 + RU * Om);
+        if (j == 1) jS = jS + DT(Tdot * invT);
       }
       J[e0 * ld + s] = jT;
       J[e1 * ld + s] = jS;
+    }
+
+    if (NEWTON) {
+      // M = I - h gamma J, in place (this thread's column only)
+      const DT hg = DT(-hstep[s] * gamma);
+      for (int64_t e = 0; e < n_out; e++) {
+        DT* p = J + e * ld + s;
+        *p = hg * __ldcg(p);
+      }
+      for (int k = 0; k < N; k++) {
+        DT* p = J + jpos<FMT>(m, k, k) * ld + s;
+        *p = *p + DT(1);
+      }
     }
   }
 }
@@ -661,6 +492,8 @@ static int num_sms() {
   }
   return g_num_sms;
 }
+
+int sm_count() { return num_sms(); }
 
 // Per-state arrays: in shared memory when 128 threads fit, else in a global
 // workspace with a fixed grid-stride grid.
@@ -721,12 +554,14 @@ int launch_source(const DevMech& m, int mode, int64_t n, const double* param, co
   return check_cuda(cudaGetLastError(), "k_source_terms launch");
 }
 
-template <int MODE, int FMT>
+template <int MODE, int FMT, typename DT = double, bool NEWTON = false>
 static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const double* param, const double* phi,
-                        int64_t ld, double* J, double* dphi, int* status, double* ws, cudaStream_t st) {
+                        int64_t ld, DT* J, double* dphi, int* status, double* ws, cudaStream_t st,
+                        const double* hstep = nullptr, double gamma = 0.0) {
   int rc;
-  if ((rc = set_smem(k_jacobian<MODE, FMT>, p.smem))) return rc;
-  k_jacobian<MODE, FMT><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, J, dphi, status, ws, p.ws_stride);
+  if ((rc = set_smem(k_jacobian<MODE, FMT, DT, NEWTON>, p.smem))) return rc;
+  k_jacobian<MODE, FMT, DT, NEWTON><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, J, dphi, status, ws,
+                                                                     p.ws_stride, hstep, gamma);
   return check_cuda(cudaGetLastError(), "k_jacobian launch");
 }
 
@@ -748,6 +583,25 @@ int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double
 }
 
 size_t workspace_bytes(int arrays, int ns, int64_t n) { return plan_for(arrays, ns, n).ws_bytes; }
+
+// Newton-iteration matrix M = I - h*gamma*J in FP32 (derivative arithmetic
+// in FP32, rates and source terms in FP64).
+int launch_newton_f32(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
+                      int64_t ld, const double* hstep, double gamma, float* M, double* dphi, int* status,
+                      void* work, size_t work_bytes, cudaStream_t st) {
+  LaunchPlan p = plan_for(jacobian_arrays(), m.ns, n);
+  if (p.global_ws && (!work || work_bytes < p.ws_bytes))
+    return fail(PJ_ERR_NOMEM, "workspace too small for the Newton-matrix kernel (see pj_workspace_size)");
+  double* ws = p.global_ws ? static_cast<double*>(work) : nullptr;
+  if (mode == PJ_CONP) {
+    if (fmt == PJ_CSR) return launch_jac_t<PJ_CONP, PJ_CSR, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+    if (fmt == PJ_CSC) return launch_jac_t<PJ_CONP, PJ_CSC, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+    return launch_jac_t<PJ_CONP, PJ_DENSE, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+  }
+  if (fmt == PJ_CSR) return launch_jac_t<PJ_CONV, PJ_CSR, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+  if (fmt == PJ_CSC) return launch_jac_t<PJ_CONV, PJ_CSC, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+  return launch_jac_t<PJ_CONV, PJ_DENSE, float, true>(m, p, n, param, phi, ld, M, dphi, status, ws, st, hstep, gamma);
+}
 
 // Run k_jacobian with its per-state arrays in a scratch region that holds
 // `scratch_threads` threads' arrays (grid-stride over the states).  Used by

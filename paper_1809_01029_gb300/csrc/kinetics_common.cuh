@@ -1,0 +1,254 @@
+// Device helpers shared by the kernels of kinetics.cu and forms.cu: state
+// loading, falloff broadening, reaction-side products, rate constants, third
+// bodies, production-rate scatter and reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kinetics_device.cuh"
+
+#ifndef PJ_DYN_SMEM
+#define PJ_DYN_SMEM extern __shared__ double smem[]
+#endif
+
+namespace pj {
+
+struct StateScalars {
+  double T, V, P, invT, lnT, Ctot;
+};
+
+// Load one state, fill C_k (k < Ns-1 as n_k/V; the bath gas as C_tot minus
+// the others summed in species order) and check validity.
+template <int MODE>
+__device__ __forceinline__ bool load_state(const DevMech& m, const double* __restrict__ phi,
+                                           const double* __restrict__ param, int64_t ld, int64_t s,
+                                           const StateArrays& A, int aC, StateScalars& st) {
+  const int ns = m.ns;
+  const double T = phi[s], S = phi[ld + s], par = param[s];
+  const double V = MODE == PJ_CONP ? S : par;
+  const double P = MODE == PJ_CONP ? par : S;
+  bool ok = (T > 0.0) && (V > 0.0) && (P > 0.0) && isfinite(T) && isfinite(V) && isfinite(P);
+  double acc = 0.0;
+  for (int k = 0; k < ns - 1; k++) {
+    const double c = phi[(int64_t)(k + 2) * ld + s] / V;
+    A.at(aC, k) = c;
+    acc += c;
+  }
+  const double Ctot = P / (RU * T);
+  const double Cns = Ctot - acc;
+  A.at(aC, ns - 1) = Cns;
+  ok = ok && isfinite(acc) && isfinite(Cns) && !(Cns < -1e-12 * Ctot);
+  st.T = T;
+  st.V = V;
+  st.P = P;
+  st.invT = 1.0 / T;
+  st.lnT = log(T);
+  st.Ctot = Ctot;
+  return ok;
+}
+
+// Troe / SRI broadening factor F(T, Pr) in FP64.  With derivatives also
+// returns FxPr = Pr dF/dPr (at fixed T) and FT = dF/dT (at fixed Pr),
+// evaluated in the derivative type DT (FP64, or FP32 for the Newton form).
+template <bool DERIV, typename DT = double>
+__device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind, double T, double invT,
+                                            double lnT, double Pr, DT& FxPr, DT& FT) {
+  FxPr = DT(0);
+  FT = DT(0);
+  if (kind == PJ_TROE) {
+    const double a = __ldg(&r->fp[0]), iT3 = __ldg(&r->fp[1]), iT1 = __ldg(&r->fp[2]);
+    const double T2 = __ldg(&r->fp[3]), has2 = __ldg(&r->fp[4]);
+    const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
+    const double e2 = has2 != 0.0 ? exp(-T2 * invT) : 0.0;
+    const double Fcent = (1.0 - a) * e3 + a * e1 + e2;
+    const double L = log10(Fcent);
+    const double x = log10(Pr);
+    const double cc = -0.4 - 0.67 * L;
+    const double NN = 0.75 - 1.27 * L;
+    const double xc = x + cc;
+    const double D = NN - 0.14 * xc;
+    const double f1 = xc / D;
+    const double g = 1.0 / (1.0 + f1 * f1);
+    const double F = exp(LN10 * (L * g));
+    if (DERIV) {
+      const DT Lt = DT(L), Dt = DT(D), f1t = DT(f1), gt = DT(g), Ft = DT(F), xct = DT(xc);
+      const DT iD = DT(1) / Dt;
+      const DT iD2 = iD * iD;
+      const DT m2fg2 = DT(-2) * f1t * gt * gt;
+      const DT dlg_dx = Lt * m2fg2 * DT(NN) * iD2;
+      const DT dlg_dL = gt + Lt * m2fg2 * (DT(-0.67) * Dt + DT(1.1762) * xct) * iD2;
+      const DT dFcent = DT(-(1.0 - a) * iT3) * DT(e3) - DT(a * iT1) * DT(e1) + DT(T2) * DT(invT * invT) * DT(e2);
+      FxPr = Ft * dlg_dx;
+      FT = Ft * dlg_dL * dFcent / DT(Fcent);
+    }
+    return F;
+  }
+  if (kind == PJ_SRI) {
+    const double a = __ldg(&r->fp[0]), b = __ldg(&r->fp[1]), ic = __ldg(&r->fp[2]);
+    const double d = __ldg(&r->fp[3]), e = __ldg(&r->fp[4]);
+    const double x = log10(Pr);
+    const double X = 1.0 / (1.0 + x * x);
+    const double eb = exp(-b * invT), ec = exp(-T * ic);
+    const double Z = a * eb + ec;
+    const double lnZ = log(Z);
+    const double F = d * exp(X * lnZ + e * lnT);
+    if (DERIV) {
+      const DT Xt = DT(X), Ft = DT(F), xt = DT(x), it = DT(invT);
+      FxPr = Ft * (DT(lnZ) * (DT(-2) * xt * Xt * Xt)) * DT(1.0 / LN10);
+      const DT dZ = DT(a * b) * it * it * DT(eb) - DT(ic) * DT(ec);
+      FT = Ft * (Xt * dZ / DT(Z) + DT(e) * it);
+    }
+    return F;
+  }
+  return 1.0;  // Lindemann
+}
+
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
+// nu * x with the common nu = +-1 done as a sign flip (integer pipe)
+__device__ __forceinline__ double nu_times(int nu, double nud, double x) {
+  if (nu == 1) return x;
+  if (nu == -1) return dneg(x);
+  return nud * x;
+}
+
+// R = k * prod_a C_a^nu_a over one reaction side (positions off .. off+n-1)
+// and, with DER, dR[a] = dR/dC_a.  The shape code selects the minimal
+// multiply sequence; SH_GEN falls back to a general product.
+template <bool DER>
+__device__ __forceinline__ double side_rate(const StateArrays& A, int aC, const Rxn* __restrict__ r, int off,
+                                            int shape, int n, double k, double (&dR)[PJ_MAX_SP]) {
+  switch (shape) {
+    case SH_1: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off]));
+      if (DER) dR[0] = k;
+      return k * c0;
+    }
+    case SH_2: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off]));
+      const double t = k * c0;
+      if (DER) dR[0] = t + t;
+      return t * c0;
+    }
+    case SH_11: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double t = k * c1;
+      if (DER) {
+        dR[0] = t;
+        dR[1] = k * c0;
+      }
+      return t * c0;
+    }
+    case SH_21: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double t = k * c0;
+      const double t1 = t * c1;
+      if (DER) {
+        dR[0] = t1 + t1;
+        dR[1] = t * c0;
+      }
+      return t1 * c0;
+    }
+    case SH_111: {
+      const double c0 = A.at(aC, __ldg(&r->sp[off])), c1 = A.at(aC, __ldg(&r->sp[off + 1]));
+      const double c2 = A.at(aC, __ldg(&r->sp[off + 2]));
+      const double t2 = k * c2;
+      const double t12 = t2 * c1;
+      if (DER) {
+        dR[0] = t12;
+        dR[1] = t2 * c0;
+        dR[2] = (k * c0) * c1;
+      }
+      return t12 * c0;
+    }
+    default: {
+      double pw[PJ_MAX_SP], dpw[PJ_MAX_SP];
+#pragma unroll
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        pw[a] = 1.0;
+        dpw[a] = 0.0;
+        if (a < n) {
+          const int v = __ldg(&r->nu[off + a]);
+          const double c = A.at(aC, __ldg(&r->sp[off + a]));
+          const double cm = powi(c, v - 1);
+          pw[a] = cm * c;
+          dpw[a] = v * cm;
+        }
+      }
+      double R = k;
+#pragma unroll
+      for (int a = 0; a < PJ_MAX_SP; a++)
+        if (a < n) R *= pw[a];
+      if (DER) {
+#pragma unroll
+        for (int a = 0; a < PJ_MAX_SP; a++) {
+          if (a >= n) continue;
+          double p = k * dpw[a];
+#pragma unroll
+          for (int b = 0; b < PJ_MAX_SP; b++)
+            if (b != a && b < n) p *= pw[b];
+          dR[a] = p;
+        }
+      }
+      return R;
+    }
+  }
+}
+
+// Forward and reverse rate constants; the two exponentials sit in one basic
+// block so their dependency chains interleave.
+__device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, const Rxn* __restrict__ r, int rev,
+                                               int nre, int npr, double lnkf, double logPRT, double& kf,
+                                               double& kr) {
+  if (rev) {
+    double dg = 0.0;
+#pragma unroll
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre) dg = fma(-__ldg(&r->nud[a]), A.at(aG, __ldg(&r->sp[a])), dg);
+      if (a < npr) dg = fma(__ldg(&r->nud[PJ_MAX_SP + a]), A.at(aG, __ldg(&r->sp[PJ_MAX_SP + a])), dg);
+    }
+    // kr = kf / Kc with Kc = exp(-dg) (P_std / R T)^dnu
+    const double larg = lnkf + dg - __ldg(&r->dnu) * logPRT;
+    kf = exp(lnkf);
+    kr = exp(larg);
+  } else {
+    kf = exp(lnkf);
+    kr = 0.0;
+  }
+}
+
+// Third-body concentration [M] = C_tot + sum_e (alpha_e - 1) C_e.
+__device__ __forceinline__ double third_body(const DevMech& m, const StateArrays& A, int aC, const Rxn* __restrict__ r,
+                                             double Ctot) {
+  double M = Ctot;
+  for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
+    M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
+  return M;
+}
+
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }  // result unused: red.global.add.f64
+
+// wdot_k += nu_k q for the reaction's species: L2 reductions into wrow[k*ld]
+// for k < Ns-1, the bath gas into a register.
+__device__ __forceinline__ void scatter_wdot(const Rxn* __restrict__ r, int nre, int npr, int bath, double q,
+                                             double* wrow, int64_t ld, double& w_bath) {
+#pragma unroll
+  for (int a = 0; a < PJ_MAX_SP; a++) {
+    if (a < nre) {
+      const int k = __ldg(&r->sp[a]);
+      const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
+      if (k == bath) w_bath -= v;
+      else red_add(wrow + (int64_t)k * ld, dneg(v));
+    }
+    if (a < npr) {
+      const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
+      const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
+      if (k == bath) w_bath += v;
+      else red_add(wrow + (int64_t)k * ld, v);
+    }
+  }
+}
+
+}  // namespace pj

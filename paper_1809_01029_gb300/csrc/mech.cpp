@@ -279,7 +279,8 @@ int mech_build(pj_mech* m) {
   const size_t o_rows = align256(o_eam + eff_am1.size() * sizeof(double));
   const size_t o_pcsr = align256(o_rows + rows.size() * sizeof(RowNu));
   const size_t o_pcsc = align256(o_pcsr + (size_t)N * N * sizeof(int32_t));
-  const size_t total = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
+  const size_t o_perm = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
+  const size_t total = align256(o_perm + (size_t)nr * sizeof(int32_t));
 
   std::vector<char> blob(total, 0);
   auto put = [&](size_t off, const void* src, size_t bytes) { if (bytes) std::memcpy(blob.data() + off, src, bytes); };
@@ -291,6 +292,7 @@ int mech_build(pj_mech* m) {
   put(o_rows, rows.data(), rows.size() * sizeof(RowNu));
   put(o_pcsr, m->pos_csr.data(), m->pos_csr.size() * sizeof(int32_t));
   put(o_pcsc, m->pos_csc.data(), m->pos_csc.size() * sizeof(int32_t));
+  put(o_perm, m->perm.data(), m->perm.size() * sizeof(int32_t));
 
   // Without any CUDA device the handle stays host-only: its pattern can be
   // queried, evaluation calls fail with PJ_ERR_CUDA.
@@ -326,6 +328,7 @@ int mech_build(pj_mech* m) {
   dm.rows = reinterpret_cast<const RowNu*>(b + o_rows);
   dm.pos_csr = reinterpret_cast<const int32_t*>(b + o_pcsr);
   dm.pos_csc = reinterpret_cast<const int32_t*>(b + o_pcsc);
+  dm.perm = reinterpret_cast<const int32_t*>(b + o_perm);
   return PJ_OK;
 }
 

@@ -74,6 +74,7 @@ struct DevMech {
   const RowNu* rows;              // [n_rows]
   const int32_t* pos_csr;         // [N*N] full -> CSR value index, -1 if absent
   const int32_t* pos_csc;         // [N*N] full -> CSC value index, -1 if absent
+  const int32_t* perm;            // [nr] kernel order -> original reaction index
 };
 
 }  // namespace pj

@@ -202,8 +202,65 @@ def other_workloads(pj, synth, torch, dev, stream):
     t = _time(torch, stream, lambda: pj.pj_vjp(h, synth.CONP, n, par, phi, n, uw, uT, y, g, gt, None, w, wb, stream),
               reps=10)
     out["gri53_64k_vjp"] = n / (t * 1e-3)
+    del y, g, gt, w, phi, par, uw, uT
     torch.cuda.empty_cache()
+    out.update(ragged_workload(pj, synth, torch, dev, stream))
     return out
+
+
+def ragged_workload(pj, synth, torch, dev, stream, group_states=140000):
+    """874 species / 3796 reactions, 32 log-uniform batches of 1,024..65,536
+    states: source terms + CSR Jacobian through one plan (persistent kernels,
+    groups of <= group_states states sharing one output pool), autotuned on a
+    sample, captured as a CUDA graph and timed by replay."""
+    import tempfile
+    m = synth.make_mechanism("ic5874")
+    h = pj.pj_mech_create(m)
+    sizes = [int(x) for x in synth.ragged_batch_sizes()]
+    N1 = m.n_species + 1
+    # group assignment as the plan does it (consecutive batches)
+    groups, cur, acc = [], [], 0
+    for b, n in enumerate(sizes):
+        if cur and acc + n > group_states:
+            groups.append(cur)
+            cur, acc = [], 0
+        cur.append(b)
+        acc += n
+    groups.append(cur)
+    pool_states = max(sum(sizes[b] for b in g) for g in groups)
+    pool = torch.empty(pool_states * h.nnz, dtype=torch.float64, device=dev)
+    fpool = torch.empty(pool_states * N1, dtype=torch.float64, device=dev)
+    batches = []
+    for g in groups:
+        off = 0
+        for b in g:
+            n = sizes[b]
+            phi_h, par_h = synth.make_states(m, n, 2018 + 5 + 7919 * b, synth.CONP)
+            phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+            o = pool[off * h.nnz:(off + n) * h.nnz].view(h.nnz, n)
+            f = fpool[off * N1:(off + n) * N1].view(N1, n)
+            batches.append((par, phi, o, f))
+            off += n
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    cache = os.path.join(tempfile.gettempdir(), "pyjac_gb_autotune.jsonl")
+    sample = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches[:6], status=status)
+    cfg = sample.autotune(stream=stream, cache_path=cache, reps=1)
+    del sample
+    plan = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches, max_states_per_launch=group_states, status=status)
+    plan.set_config(cfg["threads_per_block"], cfg["blocks_per_sm"], cfg["use_shared"])
+    gs = torch.cuda.Stream(dev)
+    plan.capture(gs)
+    plan.launch(gs)
+    gs.synchronize()
+    t = _time(torch, gs, lambda: plan.launch(gs), reps=2)
+    assert int(status.item()) == 0
+    total = sum(sizes)
+    res = {"ic5874_ragged_jacobian_csr_graph": total / (t * 1e-3),
+           "ic5874_ragged_info": {"batches": len(sizes), "states": total, "groups": len(groups),
+                                  "config": plan.config(), "ms_per_replay": t}}
+    del plan, batches, pool, fpool
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_reference(args, rank, world):

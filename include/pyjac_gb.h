@@ -245,6 +245,60 @@ int pj_vjp(const pj_mech* mech, int mode, int64_t n, const double* d_param, cons
            const double* d_u_wdot, const double* d_u_T, double* d_y, double* d_g_phi, double* d_g_theta,
            int* d_status, void* d_work, size_t work_bytes, void* stream);
 
+/* ---- batching form: uneven batches, persistent kernels, CUDA graphs ----
+ *
+ * One batch of states: its own device buffers and leading dimension (the
+ * layout of pj_eval_source_terms / pj_eval_jacobian_sparse).  d_out receives
+ * the source terms (PJ_OP_SOURCE) or the Jacobian values in `fmt` order
+ * (PJ_OP_JACOBIAN, FP64); d_dphi receives the source terms of a Jacobian
+ * plan (required there, unused otherwise). */
+typedef struct {
+  const double* d_param;
+  const double* d_phi;
+  int64_t n;
+  int64_t ld;
+  double* d_out;
+  double* d_dphi;
+} pj_batch;
+
+typedef struct pj_plan pj_plan;
+
+/* Plan the evaluation of n_batches batches (op PJ_OP_SOURCE or
+ * PJ_OP_JACOBIAN).  Consecutive batches are grouped into launches of at most
+ * max_states_per_launch states (0: one launch); in each launch a persistent
+ * kernel's warps take 32-state tiles of any batch of the group from a work
+ * counter.  Batches of different groups may share output memory (groups run
+ * one after another on the stream).  d_status (nullable) counts invalid
+ * states.  Allocates device tables and, when the per-state arrays do not fit
+ * shared memory, a workspace.  The default launch shape is the one
+ * pj_workspace_size would imply; see pj_plan_autotune. */
+int pj_plan_create(const pj_mech* mech, int op, int mode, int fmt, int n_batches, const pj_batch* batches,
+                   int64_t max_states_per_launch, int* d_status, pj_plan** out);
+int pj_plan_free(pj_plan* plan);
+
+/* Launch shape: threads per block (32, 64, 128), resident blocks per SM
+ * (1..16; the grid is blocks_per_sm x SMs), per-state arrays in shared
+ * memory (use_shared = 1) or in the plan's global workspace. */
+int pj_plan_set_config(pj_plan* plan, int threads_per_block, int blocks_per_sm, int use_shared);
+int pj_plan_get_config(const pj_plan* plan, int* threads_per_block, int* blocks_per_sm, int* use_shared,
+                       int* n_groups);
+
+/* Time every admissible launch shape on the plan's own batches (reps runs
+ * each, after one warm-up) and keep the fastest.  With cache_path non-NULL
+ * the choice is read from / appended to that file (one JSON object per line,
+ * keyed by GPU name, a hash of the mechanism constants, op, mode and fmt);
+ * a cached entry is used without timing.  Synchronises the stream. */
+int pj_plan_autotune(pj_plan* plan, void* stream, const char* cache_path, int reps);
+
+/* Run the plan on `stream` (asynchronous). */
+int pj_plan_run(pj_plan* plan, void* stream);
+
+/* Capture one run into a CUDA graph on a non-default `stream`, then replay it
+ * with pj_plan_launch (counters reset inside the graph).  Changing the launch
+ * shape drops the graph. */
+int pj_plan_capture(pj_plan* plan, void* stream);
+int pj_plan_launch(pj_plan* plan, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,7 +6,7 @@ complex128 restatement of the method and shares no code with the CUDA path.
 """
 from . import kinetics, forms
 from .kinetics import (CONP, CONV, R, R_CAL, P_ATM, concentrations, nasa7, rates, source_terms,
-                       source_terms_from_rates, jacobian, source_term_envelope, jacobian_envelope,
+                       source_terms_from_rates, jacobian, jacobian_columns, source_term_envelope, jacobian_envelope,
                        sparsity_pattern, csr_pattern, csc_pattern, dense_to_csr_values,
                        dense_to_csc_values, net_stoich, dependence_set)
 from .forms import newton_matrix, vjp, outputs_y, y_jacobian, vjp_envelope

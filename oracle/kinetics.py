@@ -299,6 +299,20 @@ def jacobian(mech, mode, phi, param, with_parts=False):
     return J
 
 
+def jacobian_columns(mech, mode, phi, param, cols):
+    """Selected Jacobian columns [N, len(cols), n] by complex step (for large
+    mechanisms where the full Jacobian is too slow for the oracle)."""
+    N = mech.n_species + 1
+    out = np.empty((N, len(cols), phi.shape[1]))
+    for c, j in enumerate(cols):
+        ph = phi.astype(np.complex128)
+        hj = _cs_step(phi[j])
+        ph[j] = ph[j] + 1j * hj
+        r = rates(mech, mode, ph, param.astype(np.complex128))
+        out[:, c] = source_terms_from_rates(mech, mode, r)[0].imag / hj
+    return out
+
+
 # ---------------------------------------------------------------------------
 # rounding envelopes for a conditioning-aware comparison (Sec. 3.2: net rates
 # of progress lose accuracy where forward and reverse rates nearly cancel)

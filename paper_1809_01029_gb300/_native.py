@@ -30,6 +30,11 @@ class pj_mech_desc(C.Structure):
                 ("sri", _dp), ("eff_ptr", _ip), ("eff_sp", _ip), ("eff_val", _dp)]
 
 
+class pj_batch(C.Structure):
+    _fields_ = [("d_param", C.c_void_p), ("d_phi", C.c_void_p), ("n", C.c_int64), ("ld", C.c_int64),
+                ("d_out", C.c_void_p), ("d_dphi", C.c_void_p)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/pyjac_gb.h
 SIGNATURES = {
     "pj_last_error": (C.c_char_p, []),
@@ -51,6 +56,16 @@ SIGNATURES = {
                          C.c_size_t, _vp]),
     "pj_newton_matrix_f32": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_double,
                                        _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pj_plan_create": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(pj_batch), C.c_int64, _vp,
+                                 C.POINTER(_vp)]),
+    "pj_plan_free": (C.c_int, [_vp]),
+    "pj_plan_set_config": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "pj_plan_get_config": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int)]),
+    "pj_plan_autotune": (C.c_int, [_vp, _vp, C.c_char_p, C.c_int]),
+    "pj_plan_run": (C.c_int, [_vp, _vp]),
+    "pj_plan_capture": (C.c_int, [_vp, _vp]),
+    "pj_plan_launch": (C.c_int, [_vp, _vp]),
     "pj_eval_jacobian_sparse_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
                                                   _vp, _vp, _vp]),
 }

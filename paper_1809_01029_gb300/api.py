@@ -320,3 +320,62 @@ def source_terms_y(mech, mode, phi, param, theta):
     if _Y is None:
         _Y = _make_function()
     return _Y.apply(phi, theta, mech, mode, param)
+
+
+# ---------------------------------------------------------------------------
+# batching form
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owner of a ``pj_plan*``: uneven batches through persistent kernels,
+    optionally replayed as a captured CUDA graph.  ``batches`` is a list of
+    (param, phi, out, dphi) tensors; phi is [Ns+1, n] with unit stride along
+    states, out/dphi as for the single-batch entry points."""
+
+    def __init__(self, mech, op, mode, batches, fmt=PJ_CSR, max_states_per_launch=0, status=None):
+        lib = N.load()
+        self.mech = mech
+        self._keep = batches
+        arr = (N.pj_batch * max(len(batches), 1))()
+        for i, (param, phi, out, dphi) in enumerate(batches):
+            n = phi.shape[1]
+            arr[i] = N.pj_batch(param.data_ptr(), phi.data_ptr(), n, max(phi.stride(0), 1), out.data_ptr(),
+                                dphi.data_ptr() if dphi is not None else None)
+        h = C.c_void_p()
+        check(lib.pj_plan_create(mech.handle, op, mode, fmt, len(batches), arr, max_states_per_launch,
+                                 _ptr(status), C.byref(h)), "pj_plan_create")
+        self._h = h
+
+    def config(self):
+        t, b, s, g = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(N.load().pj_plan_get_config(self._h, C.byref(t), C.byref(b), C.byref(s), C.byref(g)),
+              "pj_plan_get_config")
+        return dict(threads_per_block=t.value, blocks_per_sm=b.value, use_shared=s.value, groups=g.value)
+
+    def set_config(self, threads_per_block, blocks_per_sm, use_shared):
+        check(N.load().pj_plan_set_config(self._h, threads_per_block, blocks_per_sm, int(use_shared)),
+              "pj_plan_set_config")
+
+    def autotune(self, stream=None, cache_path=None, reps=2):
+        check(N.load().pj_plan_autotune(self._h, _stream(stream), cache_path.encode() if cache_path else None,
+                                        reps), "pj_plan_autotune")
+        return self.config()
+
+    def run(self, stream=None):
+        check(N.load().pj_plan_run(self._h, _stream(stream)), "pj_plan_run")
+
+    def capture(self, stream):
+        check(N.load().pj_plan_capture(self._h, _stream(stream)), "pj_plan_capture")
+
+    def launch(self, stream=None):
+        check(N.load().pj_plan_launch(self._h, _stream(stream)), "pj_plan_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and N._lib is not None:
+            N._lib.pj_plan_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -245,6 +245,12 @@ int pj_vjp(const pj_mech* mech, int mode, int64_t n, const double* d_param, cons
            const double* d_u_wdot, const double* d_u_T, double* d_y, double* d_g_phi, double* d_g_theta,
            int* d_status, void* d_work, size_t work_bytes, void* stream);
 
+/* Diagnostic: the library's FP64 exponential (Tang's table-driven method,
+ * used by every kernel for rate constants and falloff factors) and CUDA's
+ * exp for the same n device inputs, so that its error can be verified. */
+int pj_diag_exp(const pj_mech* mech, int64_t n, const double* d_x, double* d_y_ours, double* d_y_lib,
+                void* stream);
+
 /* ---- batching form: uneven batches, persistent kernels, CUDA graphs ----
  *
  * One batch of states: its own device buffers and leading dimension (the

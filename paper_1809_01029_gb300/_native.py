@@ -56,6 +56,7 @@ SIGNATURES = {
                          C.c_size_t, _vp]),
     "pj_newton_matrix_f32": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_double,
                                        _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pj_diag_exp": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "pj_plan_create": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(pj_batch), C.c_int64, _vp,
                                  C.POINTER(_vp)]),
     "pj_plan_free": (C.c_int, [_vp]),

@@ -162,6 +162,11 @@ def pj_newton_matrix_f32(mech, mode, fmt, n, param, phi, ld, h, gamma, M, dphi, 
                  "pj_newton_matrix_f32")
 
 
+def pj_diag_exp(mech, n, x, y_ours, y_lib, stream=None):
+    return check(N.load().pj_diag_exp(mech.handle, n, _ptr(x), _ptr(y_ours), _ptr(y_lib), _stream(stream)),
+                 "pj_diag_exp")
+
+
 def pj_eval_jacobian_sparse_noalloc(mech, mode, fmt, n, param, phi, ld, vals, dphi, status=None, stream=None):
     """Sparse Jacobian without a workspace argument, for callers that cannot
     allocate device memory: the library's fixed per-device scratch array is

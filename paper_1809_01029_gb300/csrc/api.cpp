@@ -14,6 +14,7 @@ int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double
                     cudaStream_t st);
 size_t workspace_bytes(int arrays, int ns, int64_t n);
 size_t form_workspace_bytes(int op, const DevMech& m, int64_t n);
+int launch_diag_exp(const DevMech& m, int64_t n, const double* x, double* y_ours, double* y_lib, cudaStream_t st);
 int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
                   double* y, int* status, void* work, size_t work_bytes, cudaStream_t st);
 int launch_vjp(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
@@ -124,4 +125,13 @@ extern "C" int pj_vjp(const pj_mech* m, int mode, int64_t n, const double* param
                          ? PJ_OK : fail(PJ_ERR_CUDA, "pj_vjp: cudaMemsetAsync failed");
   return launch_vjp(m->dm, mode, n, param, phi, ld, u_wdot, u_T, y, g_phi, g_theta, status, work, work_bytes,
                     (cudaStream_t)stream);
+}
+
+extern "C" int pj_diag_exp(const pj_mech* m, int64_t n, const double* x, double* y_ours, double* y_lib,
+                           void* stream) {
+  int rc = check_common("pj_diag_exp", m, PJ_CONP, n, n > 0 ? n : 1, x, x, y_ours);
+  if (rc) return rc;
+  if (n > 0 && !y_lib) return fail(PJ_ERR_ARG, "pj_diag_exp: null buffer");
+  if (n == 0) return PJ_OK;
+  return launch_diag_exp(m->dm, n, x, y_ours, y_lib, (cudaStream_t)stream);
 }

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(128) k_batched(DevMech m, const BatchDev* __re
                                                  unsigned long long* counter, int* status, double* ws,
                                                  int64_t ws_stride) {
   PJ_DYN_SMEM;
+  load_exp_table(m.exp_tab);
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   StateArrays A;
@@ -177,7 +178,7 @@ static int plan_configure(pj_plan* p, int tpb, int bps, int use_smem) {
   if (tpb != 32 && tpb != 64 && tpb != 128) return fail(PJ_ERR_ARG, "plan: threads per block must be 32, 64 or 128");
   if (bps < 1 || bps > 16) return fail(PJ_ERR_ARG, "plan: blocks per SM must be 1..16");
   const size_t per_thread = (size_t)plan_arrays(p) * p->mech->ns * sizeof(double);
-  const size_t smem_cap = 227 * 1024;
+  const size_t smem_cap = 225 * 1024;
   if (use_smem && per_thread * tpb > smem_cap)
     return fail(PJ_ERR_UNSUPPORTED, "plan: per-state arrays do not fit shared memory at this block size");
   drop_graph(p);
@@ -343,7 +344,7 @@ extern "C" int pj_plan_create(const pj_mech* m, int op, int mode, int fmt, int n
     // default shape: shared memory when 128 threads' arrays fit, else a global
     // workspace with 4 resident blocks of 128 per SM
     const size_t per_thread = (size_t)plan_arrays(p) * m->ns * sizeof(double);
-    const int fit = (int)((227 * 1024 / per_thread) / 32 * 32);
+    const int fit = (int)((225 * 1024 / per_thread) / 32 * 32);
     if (fit >= 128) rc = plan_configure(p, fit >= 256 ? 128 : (fit % 64 == 0 ? 64 : 32), 1, 1);
     else rc = plan_configure(p, 128, 4, 0);
   }
@@ -426,7 +427,7 @@ extern "C" int pj_plan_autotune(pj_plan* p, void* stream, const char* cache_path
   for (int tpb : {32, 64, 128})
     for (int bps : {1, 2, 4, 8})
       for (int sm : {1, 0}) {
-        if (sm && per_thread * tpb * bps > 227 * 1024) continue;
+        if (sm && per_thread * tpb * bps > 225 * 1024) continue;
         if (!sm && per_thread * (size_t)tpb * bps * sm_count() > (size_t(8) << 30)) continue;  // workspace <= 8 GiB
         cands.push_back({tpb, bps, sm});
       }

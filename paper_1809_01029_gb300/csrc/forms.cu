@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(128) k_eval_y(DevMech m, int64_t n, const doub
                                                 const double* __restrict__ phi, int64_t ld, double* __restrict__ y,
                                                 int* status, double* ws, int64_t ws_stride) {
   PJ_DYN_SMEM;
+  load_exp_table(m.exp_tab);
   const int ns = m.ns, bath = m.ns - 1;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   StateArrays A;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(128) k_eval_y(DevMech m, int64_t n, const doub
           c = M;
         } else {
           const double lnk0 = fma(__ldg(&r->beta0), lnT, __ldg(&r->lnA0)) - __ldg(&r->theta0) * invT;
-          const double Pr = exp(lnk0 - lnkf) * M;
+          const double Pr = pj_exp(lnk0 - lnkf) * M;
           double d1, d2;
           const double F = falloff_F<false>(r, kind, T, invT, lnT, Pr, d1, d2);
           c = Pr / (1.0 + Pr) * F;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
                                              double* __restrict__ gth_part, int* status, double* ws,
                                              int64_t ws_stride) {
   PJ_DYN_SMEM;
+  load_exp_table(m.exp_tab);
   const int ns = m.ns, bath = m.ns - 1, nr = m.nr;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
           const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
           const double lnk0 = fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
           const double dlnk0 = fma(theta0, invT2, beta0 * invT);
-          const double rk = exp(lnk0 - lnkf);
+          const double rk = pj_exp(lnk0 - lnkf);
           const double Pr = rk * M;
           double FxPr, FT;
           const double F = falloff_F<true>(r, kind, T, invT, lnT, Pr, FxPr, FT);
@@ -391,7 +393,7 @@ int sm_count();
 static FormPlan form_plan(int arrays, const DevMech& m, int64_t n, bool vjp) {
   FormPlan p{};
   const size_t per_thread = (size_t)arrays * m.ns * sizeof(double);
-  const size_t smem_cap = 227 * 1024;
+  const size_t smem_cap = 225 * 1024;
   const int fit = (int)((smem_cap / per_thread) / 32 * 32);
   const int64_t cap_blocks = (int64_t)sm_count() * 8;
   if (fit >= 128) {

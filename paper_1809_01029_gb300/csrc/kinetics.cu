@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
                                                       double* __restrict__ out, int* status, double* ws,
                                                       int64_t ws_stride) {
   PJ_DYN_SMEM;
+  load_exp_table(m.exp_tab);
   const int ns = m.ns;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   StateArrays A;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
                                                   int* status, double* ws, int64_t ws_stride,
                                                   const double* __restrict__ hstep, double gamma) {
   PJ_DYN_SMEM;
+  load_exp_table(m.exp_tab);
   const int ns = m.ns;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   StateArrays A;
@@ -75,7 +77,25 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     jacobian_state<MODE, FMT, DT, NEWTON>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma);
 }
 
+// pj_exp next to the library exp, for verification (pj_diag_exp).
+__global__ void k_diag_exp(const double* __restrict__ tab, int64_t n, const double* __restrict__ x,
+                           double* __restrict__ y_ours, double* __restrict__ y_lib) {
+  load_exp_table(tab);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    y_ours[i] = pj_exp(x[i]);
+    y_lib[i] = exp(x[i]);
+  }
+}
+
 #ifndef PJ_NO_LAUNCHERS
+int launch_diag_exp(const DevMech& m, int64_t n, const double* x, double* y_ours, double* y_lib, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  k_diag_exp<<<(unsigned)blocks, 256, 0, st>>>(m.exp_tab, n, x, y_ours, y_lib);
+  return check_cuda(cudaGetLastError(), "k_diag_exp launch");
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -107,7 +127,7 @@ int sm_count() { return num_sms(); }
 LaunchPlan plan_for(int arrays, int ns, int64_t n) {
   LaunchPlan p{};
   const size_t per_thread = (size_t)arrays * ns * sizeof(double);
-  const size_t smem_cap = 227 * 1024;  // opt-in dynamic shared memory per block on sm_100-class parts
+  const size_t smem_cap = 225 * 1024;  // 227 KB opt-in per block, less the 2 KB exp table
   // threads per SM that fit the per-state arrays in shared memory, as whole
   // warps; blocks of up to 128 threads so several can share an SM
   const int fit = (int)((smem_cap / per_thread) / 32 * 32);

@@ -58,8 +58,8 @@ __device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind,
   if (kind == PJ_TROE) {
     const double a = __ldg(&r->fp[0]), iT3 = __ldg(&r->fp[1]), iT1 = __ldg(&r->fp[2]);
     const double T2 = __ldg(&r->fp[3]), has2 = __ldg(&r->fp[4]);
-    const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
-    const double e2 = has2 != 0.0 ? exp(-T2 * invT) : 0.0;
+    const double e3 = pj_exp(-T * iT3), e1 = pj_exp(-T * iT1);
+    const double e2 = has2 != 0.0 ? pj_exp(-T2 * invT) : 0.0;
     const double Fcent = (1.0 - a) * e3 + a * e1 + e2;
     const double L = log10(Fcent);
     const double x = log10(Pr);
@@ -69,7 +69,7 @@ __device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind,
     const double D = NN - 0.14 * xc;
     const double f1 = xc / D;
     const double g = 1.0 / (1.0 + f1 * f1);
-    const double F = exp(LN10 * (L * g));
+    const double F = pj_exp(LN10 * (L * g));
     if (DERIV) {
       const DT Lt = DT(L), Dt = DT(D), f1t = DT(f1), gt = DT(g), Ft = DT(F), xct = DT(xc);
       const DT iD = DT(1) / Dt;
@@ -88,10 +88,10 @@ __device__ __forceinline__ double falloff_F(const Rxn* __restrict__ r, int kind,
     const double d = __ldg(&r->fp[3]), e = __ldg(&r->fp[4]);
     const double x = log10(Pr);
     const double X = 1.0 / (1.0 + x * x);
-    const double eb = exp(-b * invT), ec = exp(-T * ic);
+    const double eb = pj_exp(-b * invT), ec = pj_exp(-T * ic);
     const double Z = a * eb + ec;
     const double lnZ = log(Z);
-    const double F = d * exp(X * lnZ + e * lnT);
+    const double F = d * pj_exp(X * lnZ + e * lnT);
     if (DERIV) {
       const DT Xt = DT(X), Ft = DT(F), xt = DT(x), it = DT(invT);
       FxPr = Ft * (DT(lnZ) * (DT(-2) * xt * Xt * Xt)) * DT(1.0 / LN10);
@@ -211,10 +211,10 @@ __device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, con
     }
     // kr = kf / Kc with Kc = exp(-dg) (P_std / R T)^dnu
     const double larg = lnkf + dg - __ldg(&r->dnu) * logPRT;
-    kf = exp(lnkf);
-    kr = exp(larg);
+    kf = pj_exp(lnkf);
+    kr = pj_exp(larg);
   } else {
-    kf = exp(lnkf);
+    kf = pj_exp(lnkf);
     kr = 0.0;
   }
 }

@@ -53,4 +53,49 @@ __device__ __forceinline__ void write_nan_state(double* out, int64_t ld, int64_t
     for (int v = 0; v < rows; v++) out[(int64_t)v * ld + s] = qnan;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 exponential after P. T. P. Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15 (1989):
+//   x = (256 m + j) ln2/256 + r,  |r| <= ln2/512,
+//   exp(x) = 2^m * 2^(j/256) * (1 + p(r)),  p(r) = r + r^2/2 + r^3/6 + r^4/24,
+// with a two-part (Cody-Waite) reduction constant so that k * LN2_256_HI is
+// exact, the 256-entry table in shared memory, and the power of two applied by
+// adding m to the exponent field.  About 9 FP64 operations instead of the
+// library's ~16 issue slots; outside |x| < 704 (overflow, underflow,
+// subnormal results, NaN) it defers to the library exp.  Error <= 1 ulp,
+// checked against CUDA's exp by the diagnostic entry point pj_diag_exp.
+// Every kernel that calls pj_exp fills the table first (load_exp_table).
+// ---------------------------------------------------------------------------
+#ifndef PJ_EXP_TABLE_DECL
+__shared__ double pj_exp_tab[256];
+#define PJ_EXP_TABLE_DECL
+#endif
+
+__device__ __forceinline__ void load_exp_table(const double* __restrict__ g) {
+#ifdef PJ_EXP_TABLE_LOAD_ALL
+  for (int i = 0; i < 256; i++) pj_exp_tab[i] = g[i];
+#else
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) pj_exp_tab[i] = __ldg(g + i);
+  __syncthreads();
+#endif
+}
+
+__device__ __forceinline__ double pj_exp(double x) {
+  const double SHIFT = 6755399441055744.0;            // 1.5 * 2^52: rounds to an integer in the low bits
+  const double INV_LN2_256 = 0x1.71547652b82fep+8;    // 256 / ln 2
+  const double LN2_256_HI = 0x1.62e42fefc0000p-9;     // ln 2 / 256, 35 significant bits
+  const double LN2_256_LO = -0x1.c610ca86c3899p-45;   // ln 2 / 256 - LN2_256_HI
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40860000) return exp(x);  // |x| >= 704 or NaN
+  const double t = fma(x, INV_LN2_256, SHIFT);
+  const int k = __double2loint(t);
+  const double kd = t - SHIFT;
+  double r = fma(-kd, LN2_256_HI, x);
+  r = fma(-kd, LN2_256_LO, r);
+  const double poly = fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5);
+  const double p = fma(r * r, poly, r);
+  const double T = pj_exp_tab[k & 255];
+  const double res = fma(T, p, T);
+  return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 8) << 52));
+}
+
 }  // namespace pj

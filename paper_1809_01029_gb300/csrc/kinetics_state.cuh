@@ -51,7 +51,7 @@ __device__ __forceinline__ void source_state(const DevMech& m, const StateArrays
         c = M;
       } else {
         const double lnk0 = fma(__ldg(&r->beta0), lnT, __ldg(&r->lnA0)) - __ldg(&r->theta0) * invT;
-        const double Pr = exp(lnk0 - lnkf) * M;
+        const double Pr = pj_exp(lnk0 - lnkf) * M;
         double d1, d2;
         const double F = falloff_F<false>(r, kind, T, invT, lnT, Pr, d1, d2);
         c = Pr / (1.0 + Pr) * F;
@@ -229,7 +229,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
         const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
         const double lnk0 = fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
         const DT dlnk0 = DT(theta0) * invT2_t + DT(beta0) * invT_t;
-        const double rk = exp(lnk0 - lnkf);
+        const double rk = pj_exp(lnk0 - lnkf);
         const double Pr = rk * M;
         DT FxPr, FT;
         const double F = falloff_F<true, DT>(r, kind, T, invT, lnT, Pr, FxPr, FT);

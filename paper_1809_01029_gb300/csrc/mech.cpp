@@ -280,7 +280,11 @@ int mech_build(pj_mech* m) {
   const size_t o_pcsr = align256(o_rows + rows.size() * sizeof(RowNu));
   const size_t o_pcsc = align256(o_pcsr + (size_t)N * N * sizeof(int32_t));
   const size_t o_perm = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
-  const size_t total = align256(o_perm + (size_t)nr * sizeof(int32_t));
+  const size_t o_etab = align256(o_perm + (size_t)nr * sizeof(int32_t));
+  const size_t total = align256(o_etab + 256 * sizeof(double));
+  // 2^(j/256) in extended precision, rounded once to double
+  double etab[256];
+  for (int j = 0; j < 256; j++) etab[j] = (double)std::exp2((long double)j / 256.0L);
 
   std::vector<char> blob(total, 0);
   auto put = [&](size_t off, const void* src, size_t bytes) { if (bytes) std::memcpy(blob.data() + off, src, bytes); };
@@ -293,6 +297,7 @@ int mech_build(pj_mech* m) {
   put(o_pcsr, m->pos_csr.data(), m->pos_csr.size() * sizeof(int32_t));
   put(o_pcsc, m->pos_csc.data(), m->pos_csc.size() * sizeof(int32_t));
   put(o_perm, m->perm.data(), m->perm.size() * sizeof(int32_t));
+  put(o_etab, etab, sizeof etab);
 
   // Without any CUDA device the handle stays host-only: its pattern can be
   // queried, evaluation calls fail with PJ_ERR_CUDA.
@@ -329,6 +334,7 @@ int mech_build(pj_mech* m) {
   dm.pos_csr = reinterpret_cast<const int32_t*>(b + o_pcsr);
   dm.pos_csc = reinterpret_cast<const int32_t*>(b + o_pcsc);
   dm.perm = reinterpret_cast<const int32_t*>(b + o_perm);
+  dm.exp_tab = reinterpret_cast<const double*>(b + o_etab);
   return PJ_OK;
 }
 

@@ -75,6 +75,7 @@ struct DevMech {
   const int32_t* pos_csr;         // [N*N] full -> CSR value index, -1 if absent
   const int32_t* pos_csc;         // [N*N] full -> CSC value index, -1 if absent
   const int32_t* perm;            // [nr] kernel order -> original reaction index
+  const double* exp_tab;          // [256] 2^(j/256), correctly rounded (pj_exp)
 };
 
 }  // namespace pj

@@ -23,6 +23,8 @@
 //    load (the mapping Sec. 3.3 proposes instead of a per-entry search).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kinetics_state.cuh"
 
 namespace pj {
@@ -75,6 +77,44 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
   }
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x)
     jacobian_state<MODE, FMT, DT, NEWTON>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma);
+}
+
+// Jacobian with h_k/RT in tensor memory (C_k and g_k/RT in shared memory):
+// blocks of 128 threads (one warp per TMEM lane quadrant) allocate `ncols`
+// columns, walk the batch warp-uniformly so that the warp-collective TMEM
+// accesses stay convergent, and free the columns before exiting.
+template <int MODE, int FMT, typename DT, bool NEWTON>
+__global__ void __launch_bounds__(128) k_jacobian_tm(DevMech m, int64_t n, const double* __restrict__ param,
+                                                     const double* __restrict__ phi, int64_t ld,
+                                                     DT* __restrict__ J, double* __restrict__ dphi, int* status,
+                                                     const double* __restrict__ hstep, double gamma,
+                                                     uint32_t ncols) {
+  PJ_DYN_SMEM;
+  __shared__ uint32_t tm_base;
+  load_exp_table(m.exp_tab);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tmem_alloc(&tm_base, ncols);
+    tmem_relinquish();
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tm_row = tm_base + ((uint32_t)(32 * (warp & 3)) << 16);
+  StateArrays A;
+  A.ns = m.ns;
+  A.base = smem + threadIdx.x;
+  A.stride = blockDim.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < n; base += stride) {
+    const int64_t s = base + lane;
+    jacobian_state<MODE, FMT, DT, NEWTON, true>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma, tm_row,
+                                                s < n);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tm_base, ncols);
 }
 
 // pj_exp next to the library exp, for verification (pj_diag_exp).
@@ -181,6 +221,49 @@ int launch_source(const DevMech& m, int mode, int64_t n, const double* param, co
   return check_cuda(cudaGetLastError(), "k_source_terms launch");
 }
 
+// TMEM mode for the Jacobian: C and g/RT in shared memory for blocks of 128,
+// h/RT in TMEM.  Used when it allows more resident threads than keeping all
+// three arrays in shared memory (both capped by 168 registers x 3 blocks).
+struct TmPlan {
+  bool use;
+  uint32_t ncols;
+  size_t smem;
+};
+
+static TmPlan tm_plan(int ns) {
+  TmPlan t{false, 0, 0};
+  const size_t cap = 225 * 1024;
+  uint32_t nc = 32;
+  while (nc < 2u * (uint32_t)ns) nc <<= 1;
+  if (nc > 512) return t;
+  const size_t smem2 = (size_t)2 * ns * sizeof(double) * 128;
+  if (smem2 > cap) return t;
+  const int reg_threads = 384;
+  int blocks = (int)(cap / (smem2 + 2048));
+  if (blocks > (int)(512 / nc)) blocks = (int)(512 / nc);
+  const int tm_threads = std::min(blocks * 128, reg_threads);
+  const size_t per3 = (size_t)3 * ns * sizeof(double);
+  const int cur_threads = std::min((int)((cap / per3) / 32 * 32), reg_threads);
+  if (tm_threads > cur_threads) {
+    t.use = true;
+    t.ncols = nc;
+    t.smem = smem2;
+  }
+  return t;
+}
+
+template <int MODE, int FMT, typename DT, bool NEWTON>
+static int launch_jac_tm(const DevMech& m, const TmPlan& t, int64_t n, const double* param, const double* phi,
+                         int64_t ld, DT* J, double* dphi, int* status, cudaStream_t st, const double* hstep,
+                         double gamma) {
+  int rc;
+  if ((rc = set_smem(k_jacobian_tm<MODE, FMT, DT, NEWTON>, t.smem))) return rc;
+  const int64_t blocks = (n + 127) / 128;
+  k_jacobian_tm<MODE, FMT, DT, NEWTON><<<(unsigned)(blocks < 1 ? 1 : blocks), 128, t.smem, st>>>(
+      m, n, param, phi, ld, J, dphi, status, hstep, gamma, t.ncols);
+  return check_cuda(cudaGetLastError(), "k_jacobian_tm launch");
+}
+
 template <int MODE, int FMT, typename DT = double, bool NEWTON = false>
 static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const double* param, const double* phi,
                         int64_t ld, DT* J, double* dphi, int* status, double* ws, cudaStream_t st,
@@ -195,6 +278,17 @@ static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const 
 int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
                     int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
                     cudaStream_t st) {
+  const TmPlan t = tm_plan(m.ns);
+  if (t.use) {
+    if (mode == PJ_CONP) {
+      if (fmt == PJ_CSR) return launch_jac_tm<PJ_CONP, PJ_CSR, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+      if (fmt == PJ_CSC) return launch_jac_tm<PJ_CONP, PJ_CSC, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+      return launch_jac_tm<PJ_CONP, PJ_DENSE, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+    }
+    if (fmt == PJ_CSR) return launch_jac_tm<PJ_CONV, PJ_CSR, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+    if (fmt == PJ_CSC) return launch_jac_tm<PJ_CONV, PJ_CSC, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+    return launch_jac_tm<PJ_CONV, PJ_DENSE, double, false>(m, t, n, param, phi, ld, J, dphi, status, st, nullptr, 0.0);
+  }
   LaunchPlan p = plan_for(jacobian_arrays(), m.ns, n);
   if (p.global_ws && (!work || work_bytes < p.ws_bytes))
     return fail(PJ_ERR_NOMEM, "workspace too small for the Jacobian kernel (see pj_workspace_size)");
@@ -209,13 +303,27 @@ int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double
   return launch_jac_t<PJ_CONV, PJ_DENSE>(m, p, n, param, phi, ld, J, dphi, status, ws, st);
 }
 
-size_t workspace_bytes(int arrays, int ns, int64_t n) { return plan_for(arrays, ns, n).ws_bytes; }
+size_t workspace_bytes(int arrays, int ns, int64_t n) {
+  if (arrays == jacobian_arrays() && tm_plan(ns).use) return 0;
+  return plan_for(arrays, ns, n).ws_bytes;
+}
 
 // Newton-iteration matrix M = I - h*gamma*J in FP32 (derivative arithmetic
 // in FP32, rates and source terms in FP64).
 int launch_newton_f32(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
                       int64_t ld, const double* hstep, double gamma, float* M, double* dphi, int* status,
                       void* work, size_t work_bytes, cudaStream_t st) {
+  const TmPlan t = tm_plan(m.ns);
+  if (t.use) {
+    if (mode == PJ_CONP) {
+      if (fmt == PJ_CSR) return launch_jac_tm<PJ_CONP, PJ_CSR, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+      if (fmt == PJ_CSC) return launch_jac_tm<PJ_CONP, PJ_CSC, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+      return launch_jac_tm<PJ_CONP, PJ_DENSE, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+    }
+    if (fmt == PJ_CSR) return launch_jac_tm<PJ_CONV, PJ_CSR, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+    if (fmt == PJ_CSC) return launch_jac_tm<PJ_CONV, PJ_CSC, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+    return launch_jac_tm<PJ_CONV, PJ_DENSE, float, true>(m, t, n, param, phi, ld, M, dphi, status, st, hstep, gamma);
+  }
   LaunchPlan p = plan_for(jacobian_arrays(), m.ns, n);
   if (p.global_ws && (!work || work_bytes < p.ws_bytes))
     return fail(PJ_ERR_NOMEM, "workspace too small for the Newton-matrix kernel (see pj_workspace_size)");

@@ -98,4 +98,40 @@ __device__ __forceinline__ double pj_exp(double x) {
   return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 8) << 52));
 }
 
+// ---------------------------------------------------------------------------
+// Tensor memory (TMEM) as per-thread storage.  A CTA of 128 threads allocates
+// `ncols` 32-bit columns across the SM's 128 TMEM lanes; thread t of warp w
+// owns lane 32*(w%4) + (t%32), so element c of its row is at
+// base + ((32*(w%4)) << 16) + c.  Warps read and write their 32 lanes with
+// warp-collective tcgen05.ld / tcgen05.st of one (warp-uniform) column pair,
+// the access pattern of per-state arrays indexed by a reaction's species.
+// ---------------------------------------------------------------------------
+#ifndef PJ_TMEM_EMU
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st_f64(uint32_t taddr, double v) {
+  const uint32_t lo = (uint32_t)__double2loint(v), hi = (uint32_t)__double2hiint(v);
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(lo), "r"(hi) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// load one double and wait for it (the wait names the registers so that no
+// use can be scheduled before it)
+__device__ __forceinline__ double tmem_ld_f64(uint32_t taddr) {
+  uint32_t lo, hi;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(taddr) : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(lo), "+r"(hi)::"memory");
+  return __hiloint2double((int)hi, (int)lo);
+}
+#endif
+
 }  // namespace pj

@@ -131,29 +131,55 @@ __device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
 // Shared memory holds C_k, g_k/RT and h_k/RT per state.  Production rates go
 // to the source-term output by L2 reductions (bath gas in a register);
 // Jacobian entries to the zero-initialised output by L2 reductions.
-// One state of the Jacobian evaluation (s < n, arrays A of this thread).
-template <int MODE, int FMT, typename DT, bool NEWTON>
+// One state of the Jacobian evaluation (arrays A of this thread).
+//
+// TM = false: s < n, h_k/RT in A (array 2); an invalid state returns early.
+// TM = true: h_k/RT lives in this thread's TMEM row at tm_row (columns
+// 2k, 2k+1) and every lane of the warp runs the whole body convergently (the
+// TMEM accesses are warp-collective): a lane past the batch (act = false) or
+// with an invalid state computes on a harmless dummy state with every global
+// read and write of the batch masked.
+template <int MODE, int FMT, typename DT, bool NEWTON, bool TM = false>
 __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArrays& A,
                                                const double* __restrict__ param, const double* __restrict__ phi,
                                                int64_t ld, int64_t s, DT* __restrict__ J, double* __restrict__ dphi,
-                                               int* status, const double* __restrict__ hstep, double gamma) {
+                                               int* status, const double* __restrict__ hstep, double gamma,
+                                               uint32_t tm_row = 0, bool act = true) {
   const int ns = m.ns, N = m.N, bath = m.ns - 1;
   const int64_t n_out = FMT == PJ_DENSE ? (int64_t)N * N : (int64_t)m.nnz;
   enum { aC = 0, aG = 1, aH = 2 };
   StateScalars st;
-  if (!load_state<MODE>(m, phi, param, ld, s, A, aC, st)) {
+  const bool ok = act && load_state<MODE>(m, phi, param, ld, s, A, aC, st);
+  if (act && !ok) {
     const DT qnan = DT(__longlong_as_double(0x7ff8000000000000ULL));
     for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = qnan;
     write_nan_state(dphi, ld, s, ns + 1);
     if (status) atomicAdd(status, 1);
-    return;
   }
+  if (!ok) {
+    if (!TM) return;
+    st.T = 1000.0;
+    st.V = 1.0;
+    st.P = 1e5;
+    st.invT = 1e-3;
+    st.lnT = log(1000.0);
+    st.Ctot = st.P / (RU * st.T);
+    for (int k = 0; k < ns; k++) A.at(aC, k) = st.Ctot / ns;
+  }
+  const bool w = ok;  // this lane reads and writes the batch
+  auto h_at = [&](int k) -> double {
+    if (TM) return tmem_ld_f64(tm_row + 2u * (uint32_t)k);
+    return A.at(aH, k);
+  };
   const double T = st.T, V = st.V, P = st.P, invT = st.invT, lnT = st.lnT, Ctot = st.Ctot;
   const double invT2 = invT * invT, invV = 1.0 / V;
   const DT invT_t = DT(invT), invT2_t = DT(invT2), invV_t = DT(invV), V_t = DT(V);
-  for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = DT(0);
+  if (w)
+    for (int64_t e = 0; e < n_out; e++) J[e * ld + s] = DT(0);
   double* __restrict__ wrow = dphi + 2 * ld + s;  // wdot_k accumulates at wrow[k*ld]
-  for (int k = 0; k < ns - 1; k++) wrow[(int64_t)k * ld] = 0.0;
+  if (w)
+    for (int k = 0; k < ns - 1; k++) wrow[(int64_t)k * ld] = 0.0;
+  if (TM) __syncwarp();
 
   // thermo, energy-equation denominator D = sum_k C_k Cx_k and dD/dT
   double den = 0.0, dden_T = 0.0, Cx_bath = 0.0;
@@ -163,13 +189,15 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
     nasa_eval(cb, T, invT, lnT, cp, h, sr);
     nasa_cp(cb, T, cp2, dcp);
     A.at(aG, k) = h - sr;
-    A.at(aH, k) = h;
+    if (TM) tmem_st_f64(tm_row + 2u * (uint32_t)k, h);
+    else A.at(aH, k) = h;
     const double Ck = A.at(aC, k);
     const double cx = MODE == PJ_CONP ? cp : cp - 1.0;
     den = fma(Ck, cx, den);
     dden_T = fma(Ck, dcp, dden_T);
     if (k == bath) Cx_bath = RU * cx;
   }
+  if (TM) tmem_wait_st();
   den *= RU;
   const double C_bath = A.at(aC, bath);
   // derivatives of the bath-gas concentration
@@ -196,10 +224,11 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
     double kf, kr;
     rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
     double dh = 0.0;
+    if (TM) __syncwarp();
 #pragma unroll
     for (int a = 0; a < PJ_MAX_SP; a++) {
-      if (a < nre) dh = fma(-__ldg(&r->nud[a]), A.at(aH, __ldg(&r->sp[a])), dh);
-      if (a < npr) dh = fma(__ldg(&r->nud[PJ_MAX_SP + a]), A.at(aH, __ldg(&r->sp[PJ_MAX_SP + a])), dh);
+      if (a < nre) dh = fma(-__ldg(&r->nud[a]), h_at(__ldg(&r->sp[a])), dh);
+      if (a < npr) dh = fma(__ldg(&r->nud[PJ_MAX_SP + a]), h_at(__ldg(&r->sp[PJ_MAX_SP + a])), dh);
     }
     double dRf[PJ_MAX_SP], dRr[PJ_MAX_SP];
     const double Rf = side_rate<true>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dRf);
@@ -286,13 +315,13 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
         const int k = __ldg(&r->sp[a]);
         const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
         if (k == bath) w_bath -= v;
-        else red_add(wrow + (int64_t)k * ld, dneg(v));
+        else if (w) red_add(wrow + (int64_t)k * ld, dneg(v));
       }
       if (a < npr) {
         const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
         const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
         if (k == bath) w_bath += v;
-        else red_add(wrow + (int64_t)k * ld, v);
+        else if (w) red_add(wrow + (int64_t)k * ld, v);
       }
     }
 
@@ -308,8 +337,8 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
     const DT VdqdT = V_t * dqdT, VdqdS = V_t * dqdS;
     for (int q2 = row_lo; q2 < row_hi; q2++) {
       const RowNu rn = m.rows[q2];
-      jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdT));
-      jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
+      if (w) jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdT));
+      if (w) jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
     }
 
     // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i
@@ -321,10 +350,10 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
       }
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
-        jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times_t<DT>(rn.nu, rn.nud, val));
+        if (w) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times_t<DT>(rn.nu, rn.nud, val));
       }
-      jred(J, jpos<FMT>(m, 0, j + 2), ld, s, dE * val);
-      jred(J, jpos<FMT>(m, 1, j + 2), ld, s, dW * val);
+      if (w) jred(J, jpos<FMT>(m, 0, j + 2), ld, s, dE * val);
+      if (w) jred(J, jpos<FMT>(m, 1, j + 2), ld, s, dW * val);
     };
 #pragma unroll
     for (int a = 0; a < PJ_MAX_SP; a++) {
@@ -340,7 +369,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
         const DT v = nu_times_t<DT>(rn.nu, rn.nud, Bi);
-        for (int j = 0; j < ns - 1; j++) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
+        for (int j = 0; j < ns - 1; j++) if (w) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
       }
       ATB = ATB + dE * Bi;
       ASB = ASB + dW * Bi;
@@ -348,26 +377,30 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
   }
 
   // source terms; the G array now holds Cx_k = R (cp_k or cv_k)
+  if (TM) __syncwarp();
   double num = 0.0, Om = 0.0, sumCxW = 0.0;
   for (int k = 0; k < ns; k++) {
     double cp, dcp;
     nasa_cp(nasa_block(m, k, T), T, cp, dcp);
     const double cx = RU * (MODE == PJ_CONP ? cp : cp - 1.0);
     A.at(aG, k) = cx;
-    const double wk = k < bath ? __ldcg(wrow + (int64_t)k * ld) : w_bath;
-    num = fma(MODE == PJ_CONP ? A.at(aH, k) : A.at(aH, k) - 1.0, wk, num);
+    const double wk = k < bath ? (w ? __ldcg(wrow + (int64_t)k * ld) : 0.0) : w_bath;
+    const double hk = h_at(k);
+    num = fma(MODE == PJ_CONP ? hk : hk - 1.0, wk, num);
     sumCxW = fma(cx, wk, sumCxW);
     if (k < bath) {
       Om = fma(__ldg(m.wfac + k), wk, Om);
-      wrow[(int64_t)k * ld] = V * wk;
-      if (MODE == PJ_CONP) jred(J, jpos<FMT>(m, k + 2, 1), ld, s, DT(wk));
+      if (w) wrow[(int64_t)k * ld] = V * wk;
+      if (MODE == PJ_CONP) if (w) jred(J, jpos<FMT>(m, k + 2, 1), ld, s, DT(wk));
     }
   }
   num *= RU * T;
   const double Tdot = -num / den;
   const double Sdot = MODE == PJ_CONP ? V * Tdot * invT + (RU * T * V / P) * Om : P * Tdot * invT + RU * T * Om;
-  dphi[s] = Tdot;
-  dphi[ld + s] = Sdot;
+  if (w) {
+    dphi[s] = Tdot;
+    dphi[ld + s] = Sdot;
+  }
 
   // energy row 0 and state row 1
   const DT iden = DT(1.0 / den);
@@ -384,8 +417,8 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
       jT = -(AT_S + Tdot_t * DT(dden_S)) * iden;
       dOm = AS_S;
     } else {
-      const DT accT = __ldcg(J + e0 * ld + s);
-      const DT accS = __ldcg(J + e1 * ld + s);
+      const DT accT = w ? __ldcg(J + e0 * ld + s) : DT(0);
+      const DT accS = w ? __ldcg(J + e1 * ld + s) : DT(0);
       jT = -(accT + ATB + Tdot_t * (DT(A.at(aG, j - 2)) - Cx_b)) * (invV_t * iden);
       dOm = (accS + ASB) * invV_t;
     }
@@ -399,11 +432,13 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArra
       if (j == 0) jS = jS + DT(-P * Tdot * invT2 + RU * Om);
       if (j == 1) jS = jS + DT(Tdot * invT);
     }
-    J[e0 * ld + s] = jT;
-    J[e1 * ld + s] = jS;
+    if (w) {
+      J[e0 * ld + s] = jT;
+      J[e1 * ld + s] = jS;
+    }
   }
 
-  if (NEWTON) {
+  if (NEWTON && w) {
     // M = I - h gamma J, in place (this thread's column only)
     const DT hg = DT(-hstep[s] * gamma);
     for (int64_t e = 0; e < n_out; e++) {

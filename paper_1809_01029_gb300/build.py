@@ -18,6 +18,14 @@ LIB = os.path.join(LIBDIR, "libpyjac_gb.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mech.cpp", "api.cpp", "kinetics.cu", "noalloc.cu", "forms.cu", "batch.cu", "hostio.cpp"]
+# jacobian_inst.cu is compiled once per (layout, precision): object name,
+# then its defines (see the file's header)
+JAC_INSTANCES = [
+    (f"jac_{lay}_{prec}", {"PJ_INST_TM": tm, "PJ_INST_F32": int(prec == "f32"),
+                           "PJ_INST_NAME": f"launch_jac_{lay}_{prec}"})
+    for lay, tm in (("plain", -1), ("tm0", 0), ("tm1", 1), ("tm2", 2))
+    for prec in ("f64", "f32")
+]
 
 
 def nvcc() -> str:
@@ -40,9 +48,11 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def _compile(src: str) -> str:
-    obj = os.path.join(BUILD, src + ".o")
+def _compile(job) -> str:
+    src, name, defs = job
+    obj = os.path.join(BUILD, name + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+           *[f"-D{k}={v}" for k, v in defs.items()],
            "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -56,10 +66,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    jobs = [(s, s, {}) for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    jobs += [("jacobian_inst.cu", name, defs) for name, defs in JAC_INSTANCES]
     t0 = time.time()
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(_compile, srcs))
+    with ThreadPoolExecutor(max_workers=min(len(jobs), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(_compile, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

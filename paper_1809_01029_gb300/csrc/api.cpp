@@ -4,27 +4,10 @@
 
 #include <string>
 
+#include "launch.h"
 #include "pj_internal.h"
 
 namespace pj {
-int launch_source(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
-                  double* out, int* status, void* work, size_t work_bytes, cudaStream_t st);
-int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
-                    int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
-                    cudaStream_t st);
-size_t workspace_bytes(int arrays, int ns, int64_t n);
-size_t form_workspace_bytes(int op, const DevMech& m, int64_t n);
-int launch_diag_exp(const DevMech& m, int64_t n, const double* x, double* y_ours, double* y_lib, cudaStream_t st);
-int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
-                  double* y, int* status, void* work, size_t work_bytes, cudaStream_t st);
-int launch_vjp(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
-               const double* u_wdot, const double* u_T, double* y, double* g_phi, double* g_theta, int* status,
-               void* work, size_t work_bytes, cudaStream_t st);
-int launch_newton_f32(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
-                      int64_t ld, const double* hstep, double gamma, float* M, double* dphi, int* status,
-                      void* work, size_t work_bytes, cudaStream_t st);
-int source_arrays();
-int jacobian_arrays();
 
 int check_common(const char* fn, const pj_mech* m, int mode, int64_t n, int64_t ld, const void* param,
                  const void* phi, const void* out) {

@@ -22,12 +22,8 @@
 #include <vector>
 
 #include "kinetics_state.cuh"
+#include "launch.h"
 
-namespace pj {
-int sm_count();
-int source_arrays();
-int jacobian_arrays();
-}  // namespace pj
 
 struct pj_plan {
   const pj_mech* mech = nullptr;
@@ -118,12 +114,7 @@ static int launch_group(const pj_plan* p, const pj_plan::Group& g, cudaStream_t 
 
 template <int OP, int MODE, int FMT>
 static int set_kernel_smem(size_t smem) {
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_batched<OP, MODE, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(k_batched)");
-  }
-  return PJ_OK;
+  return set_smem(k_batched<OP, MODE, FMT>, smem);
 }
 
 // dispatch over (op, mode, fmt)

@@ -376,6 +376,9 @@ __global__ void k_vjp_reduce(int nr, int64_t n_warps, const double* __restrict__
 }
 
 #ifndef PJ_NO_LAUNCHERS
+}  // namespace pj
+#include "launch.h"
+namespace pj {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -388,7 +391,6 @@ struct FormPlan {
   size_t part_bytes;    // VJP per-warp partials
 };
 
-int sm_count();
 
 static FormPlan form_plan(int arrays, const DevMech& m, int64_t n, bool vjp) {
   FormPlan p{};
@@ -427,14 +429,6 @@ size_t form_workspace_bytes(int op, const DevMech& m, int64_t n) {
   return p.ws_bytes;
 }
 
-template <typename K>
-static int set_smem_attr(K kern, size_t smem) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute");
-  }
-  return PJ_OK;
-}
 
 int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
                   double* y, int* status, void* work, size_t work_bytes, cudaStream_t st) {
@@ -444,10 +438,10 @@ int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, co
   double* ws = p.global_ws ? static_cast<double*>(work) : nullptr;
   int rc;
   if (mode == PJ_CONP) {
-    if ((rc = set_smem_attr(k_eval_y<PJ_CONP>, p.smem))) return rc;
+    if ((rc = set_smem(k_eval_y<PJ_CONP>, p.smem))) return rc;
     k_eval_y<PJ_CONP><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, y, status, ws, p.ws_stride);
   } else {
-    if ((rc = set_smem_attr(k_eval_y<PJ_CONV>, p.smem))) return rc;
+    if ((rc = set_smem(k_eval_y<PJ_CONV>, p.smem))) return rc;
     k_eval_y<PJ_CONV><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, y, status, ws, p.ws_stride);
   }
   return check_cuda(cudaGetLastError(), "k_eval_y launch");
@@ -466,11 +460,11 @@ int launch_vjp(const DevMech& m, int mode, int64_t n, const double* param, const
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(vjp partials)");
   int rc;
   if (mode == PJ_CONP) {
-    if ((rc = set_smem_attr(k_vjp<PJ_CONP>, p.smem))) return rc;
+    if ((rc = set_smem(k_vjp<PJ_CONP>, p.smem))) return rc;
     k_vjp<PJ_CONP><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, u_wdot, u_T, y, g_phi, part, status, ws,
                                                   p.ws_stride);
   } else {
-    if ((rc = set_smem_attr(k_vjp<PJ_CONV>, p.smem))) return rc;
+    if ((rc = set_smem(k_vjp<PJ_CONV>, p.smem))) return rc;
     k_vjp<PJ_CONV><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, u_wdot, u_T, y, g_phi, part, status, ws,
                                                   p.ws_stride);
   }

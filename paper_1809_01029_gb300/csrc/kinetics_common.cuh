@@ -19,10 +19,10 @@ struct StateScalars {
 
 // Load one state, fill C_k (k < Ns-1 as n_k/V; the bath gas as C_tot minus
 // the others summed in species order) and check validity.
-template <int MODE>
+template <int MODE, class SA>
 __device__ __forceinline__ bool load_state(const DevMech& m, const double* __restrict__ phi,
                                            const double* __restrict__ param, int64_t ld, int64_t s,
-                                           const StateArrays& A, int aC, StateScalars& st) {
+                                           const SA& A, int aC, StateScalars& st) {
   const int ns = m.ns;
   const double T = phi[s], S = phi[ld + s], par = param[s];
   const double V = MODE == PJ_CONP ? S : par;
@@ -117,8 +117,8 @@ __device__ __forceinline__ double nu_times(int nu, double nud, double x) {
 // R = k * prod_a C_a^nu_a over one reaction side (positions off .. off+n-1)
 // and, with DER, dR[a] = dR/dC_a.  The shape code selects the minimal
 // multiply sequence; SH_GEN falls back to a general product.
-template <bool DER>
-__device__ __forceinline__ double side_rate(const StateArrays& A, int aC, const Rxn* __restrict__ r, int off,
+template <bool DER, class SA>
+__device__ __forceinline__ double side_rate(const SA& A, int aC, const Rxn* __restrict__ r, int off,
                                             int shape, int n, double k, double (&dR)[PJ_MAX_SP]) {
   switch (shape) {
     case SH_1: {
@@ -199,7 +199,8 @@ __device__ __forceinline__ double side_rate(const StateArrays& A, int aC, const 
 
 // Forward and reverse rate constants; the two exponentials sit in one basic
 // block so their dependency chains interleave.
-__device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, const Rxn* __restrict__ r, int rev,
+template <class SA>
+__device__ __forceinline__ void rate_constants(const SA& A, int aG, const Rxn* __restrict__ r, int rev,
                                                int nre, int npr, double lnkf, double logPRT, double& kf,
                                                double& kr) {
   if (rev) {
@@ -220,7 +221,8 @@ __device__ __forceinline__ void rate_constants(const StateArrays& A, int aG, con
 }
 
 // Third-body concentration [M] = C_tot + sum_e (alpha_e - 1) C_e.
-__device__ __forceinline__ double third_body(const DevMech& m, const StateArrays& A, int aC, const Rxn* __restrict__ r,
+template <class SA>
+__device__ __forceinline__ double third_body(const DevMech& m, const SA& A, int aC, const Rxn* __restrict__ r,
                                              double Ctot) {
   double M = Ctot;
   for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)

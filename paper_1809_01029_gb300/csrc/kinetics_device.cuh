@@ -10,12 +10,23 @@ namespace pj {
 // Per-state working arrays: element (a, k) of the calling thread's state sits
 // at base[(a*ns + k) * stride].  base/stride point either into shared memory
 // (stride = blockDim.x) or into a global workspace (stride = total threads).
-struct StateArrays {
+// Per-state arrays of one thread (C_k, g_k/RT, h_k/RT, ...): array a of
+// species k sits at base[(a*ns + k)*stride] for a < SPLIT and at
+// base2[((a - SPLIT)*ns + k)*stride2] otherwise, so a kernel can keep the
+// first arrays in shared memory and the rest in a global workspace.  Array
+// indices are compile-time constants at every use, so the choice folds away.
+template <int SPLIT>
+struct StateArraysT {
   double* base;
   int64_t stride;
   int ns;
-  __device__ __forceinline__ double& at(int a, int k) const { return base[(int64_t)(a * ns + k) * stride]; }
+  double* base2;
+  int64_t stride2;
+  __device__ __forceinline__ double& at(int a, int k) const {
+    return a < SPLIT ? base[(int64_t)(a * ns + k) * stride] : base2[(int64_t)((a - SPLIT) * ns + k) * stride2];
+  }
 };
+using StateArrays = StateArraysT<8>;
 
 // NASA-7 block of species k for temperature T (low range iff T < T_mid).
 __device__ __forceinline__ const double* nasa_block(const DevMech& m, int k, double T) {

@@ -8,8 +8,8 @@
 namespace pj {
 
 // One state of the source-term evaluation (s < n, arrays A of this thread).
-template <int MODE>
-__device__ __forceinline__ void source_state(const DevMech& m, const StateArrays& A, const double* __restrict__ param,
+template <int MODE, class SA>
+__device__ __forceinline__ void source_state(const DevMech& m, const SA& A, const double* __restrict__ param,
                                              const double* __restrict__ phi, int64_t ld, int64_t s,
                                              double* __restrict__ out, int* status) {
   const int ns = m.ns, bath = m.ns - 1;
@@ -139,8 +139,8 @@ __device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
 // TMEM accesses are warp-collective): a lane past the batch (act = false) or
 // with an invalid state computes on a harmless dummy state with every global
 // read and write of the batch masked.
-template <int MODE, int FMT, typename DT, bool NEWTON, bool TM = false>
-__device__ __forceinline__ void jacobian_state(const DevMech& m, const StateArrays& A,
+template <int MODE, int FMT, typename DT, bool NEWTON, bool TM = false, class SA = StateArrays>
+__device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
                                                const double* __restrict__ param, const double* __restrict__ phi,
                                                int64_t ld, int64_t s, DT* __restrict__ J, double* __restrict__ dphi,
                                                int* status, const double* __restrict__ hstep, double gamma,

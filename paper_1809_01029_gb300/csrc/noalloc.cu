@@ -14,16 +14,9 @@
 #include <mutex>
 #include <string>
 
+#include "launch.h"
 #include "pj_internal.h"
 
-namespace pj {
-int check_common(const char* fn, const pj_mech* m, int mode, int64_t n, int64_t ld, const void* param,
-                 const void* phi, const void* out);
-int launch_jacobian_on_scratch(const DevMech& m, int mode, int fmt, int64_t n, const double* param,
-                               const double* phi, int64_t ld, double* J, double* dphi, int* status,
-                               double* scratch, int64_t scratch_threads, cudaStream_t st);
-int jacobian_arrays();
-}  // namespace pj
 
 namespace {
 

@@ -144,7 +144,7 @@ def sri_F(mech, i, T, Pr):
     return d * (a * np.exp(-b / T) + np.exp(-T / c)) ** X * T ** e
 
 
-def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
+def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_bath=False):
     """All intermediate quantities of the source-term evaluation.
 
     Returns a dict with T, V, P, C, Ctot, cp, h, s (NASA-7 forms), kf, kr,
@@ -155,6 +155,15 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
     parameters (used to differentiate with respect to them); dC is added to
     the concentrations after they are formed (used to differentiate with
     respect to a single concentration).
+
+    freeze_bath=True gives the rates behind the approximate Jacobian
+    (Sec. 3.4, "Sparsity patterns"): the values are unchanged, but the rates
+    of progress see the bath gas through Re(C_Ns) only, and the third-body
+    concentration is [M] = alpha . C_rate + (C_Ns - Re C_Ns), C_rate being C
+    with Re(C_Ns) in the bath-gas slot: a perturbation of C_Ns enters [M] with
+    unit efficiency.  Under a complex-step perturbation of a species amount
+    n_j (C_tot real) the rates of progress then see no change of C_Ns and
+    d[M]/dn_j = (alpha_j - 1)/V instead of (alpha_j - alpha_Ns)/V.
     """
     A = mech.A if A is None else A
     beta = mech.beta if beta is None else beta
@@ -162,6 +171,10 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
     T, V, P, C, Ctot = concentrations(mech, mode, phi, param)
     if dC is not None:
         C = C + dC
+    Cr = C                                      # concentrations seen by the rates of progress
+    if freeze_bath:
+        Cr = C.copy()
+        Cr[-1] = _re(C[-1])
     cp, h, s = nasa7(mech, T)
     g = h - s                                   # g/RT
     nu = net_stoich(mech)
@@ -186,8 +199,10 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
         if kind == ELEMENTARY:
             cmod[i] = 1.0
         else:
-            M = third_body_alpha(mech, i) @ C.reshape(ns, -1)
+            M = third_body_alpha(mech, i) @ Cr.reshape(ns, -1)
             M = M.reshape(np.shape(T))
+            if freeze_bath:
+                M = M + (C[ns - 1] - Cr[ns - 1])
             if kind == THIRD_BODY:
                 cmod[i] = M
             else:
@@ -205,10 +220,10 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None):
                 cmod[i] = F / (1 + 1 / Pr)
         fwd = kf[i]
         for k, v in mech.reactants(i):
-            fwd = fwd * C[k] ** v
+            fwd = fwd * Cr[k] ** v
         rev = kr[i]
         for k, v in mech.products(i):
-            rev = rev * C[k] ** v
+            rev = rev * Cr[k] ** v
         Rf[i], Rr[i] = fwd, rev
     qf = cmod * Rf
     qr = cmod * Rr
@@ -267,7 +282,10 @@ def _cs_step(x):
     return 1e-30 * np.maximum(np.abs(x), 1.0)
 
 
-def jacobian(mech, mode, phi, param, with_parts=False):
+EXACT, APPROX = "exact", "approx"
+
+
+def jacobian(mech, mode, phi, param, with_parts=False, form=EXACT):
     """Dense Jacobian [Ns+1, Ns+1, n] of f with P (CONP) or V (CONV) fixed.
 
     Column j is Im f(Phi + i h e_j) / h with h = 1e-30 max(|Phi_j|, 1):
@@ -277,7 +295,17 @@ def jacobian(mech, mode, phi, param, with_parts=False):
     With with_parts=True also returns the complex-step derivatives of the
     forward/reverse parts (qf, qr), of the energy-equation denominator and the
     values needed to bound rounding of a correct FP64 implementation.
+
+    form=APPROX gives the approximate Jacobian of Sec. 3.4 ("Sparsity
+    patterns"): in the species columns the derivatives that reach the rates
+    of progress through the bath-gas concentration C_Ns = C_tot - sum C_k, and
+    the pressure-modification derivatives that a non-unit bath-gas
+    efficiency spreads over every species, are left out (rates(freeze_bath=
+    True)).  The T and S columns, and every other use of C_Ns (the heat
+    capacity of the mixture), stay exact.
     """
+    if form not in (EXACT, APPROX):
+        raise ValueError(f"unknown Jacobian form {form!r}")
     N = mech.n_species + 1
     n = phi.shape[1]
     J = np.empty((N, N, n))
@@ -287,7 +315,7 @@ def jacobian(mech, mode, phi, param, with_parts=False):
         ph = phi.astype(np.complex128)
         hj = _cs_step(phi[j])
         ph[j] = ph[j] + 1j * hj
-        r = rates(mech, mode, ph, param.astype(np.complex128))
+        r = rates(mech, mode, ph, param.astype(np.complex128), freeze_bath=(form == APPROX and j >= 2))
         f, aux = source_terms_from_rates(mech, mode, r)
         J[:, j] = f.imag / hj
         if with_parts:
@@ -299,7 +327,7 @@ def jacobian(mech, mode, phi, param, with_parts=False):
     return J
 
 
-def jacobian_columns(mech, mode, phi, param, cols):
+def jacobian_columns(mech, mode, phi, param, cols, form=EXACT):
     """Selected Jacobian columns [N, len(cols), n] by complex step (for large
     mechanisms where the full Jacobian is too slow for the oracle)."""
     N = mech.n_species + 1
@@ -308,7 +336,7 @@ def jacobian_columns(mech, mode, phi, param, cols):
         ph = phi.astype(np.complex128)
         hj = _cs_step(phi[j])
         ph[j] = ph[j] + 1j * hj
-        r = rates(mech, mode, ph, param.astype(np.complex128))
+        r = rates(mech, mode, ph, param.astype(np.complex128), freeze_bath=(form == APPROX and j >= 2))
         out[:, c] = source_terms_from_rates(mech, mode, r)[0].imag / hj
     return out
 
@@ -421,13 +449,15 @@ def jacobian_envelope(mech, mode, phi, param):
 # ---------------------------------------------------------------------------
 # sparsity pattern (Sec. 3.3)
 # ---------------------------------------------------------------------------
-def dependence_set(mech, i):
+def dependence_set(mech, i, form=EXACT):
     """Species j < Ns-1 on which the rate of progress of reaction i depends.
 
     Reactants; products if reversible; for third-body / falloff reactions the
     species whose efficiency differs from the bath gas's; and every species
     when the bath gas takes part in the rate (as a reactant, as a product of a
     reversible reaction) or has a non-unit efficiency (Sec. 3.3).
+    For the approximate form (Sec. 3.4) the last clause is dropped and the
+    efficiencies are compared with the default 1 instead of the bath gas's.
     """
     ns = mech.n_species
     bath = ns - 1
@@ -439,20 +469,22 @@ def dependence_set(mech, i):
     dense = bath in members
     if mech.kind[i] != ELEMENTARY:
         a = third_body_alpha(mech, i)
-        dep.update(k for k in range(ns - 1) if a[k] != a[bath])
+        ref = 1.0 if form == APPROX else a[bath]
+        dep.update(k for k in range(ns - 1) if a[k] != ref)
         if a[bath] != 1.0:
             dense = True
-    if dense:
+    if dense and form != APPROX:
         dep.update(range(ns - 1))
     return dep
 
 
-def sparsity_pattern(mech):
-    """Boolean mask [N, N] of the exact Jacobian's structural nonzeros.
+def sparsity_pattern(mech, form=EXACT):
+    """Boolean mask [N, N] of the Jacobian's structural nonzeros.
 
     Rows/columns 0 (T) and 1 (V or P) are dense and the diagonal is kept; a
     species row k has column j when some reaction changes k (nu_ki != 0) and
-    its rate depends on j (Sec. 3.3).  Identical for CONP and CONV.
+    its rate depends on j (Sec. 3.3; for form=APPROX the dependence of
+    Sec. 3.4's approximate form).  Identical for CONP and CONV.
     """
     ns, N = mech.n_species, mech.n_species + 1
     nu = net_stoich(mech)
@@ -461,7 +493,7 @@ def sparsity_pattern(mech):
     mask[:, 0] = mask[:, 1] = True
     mask[np.arange(N), np.arange(N)] = True
     for i in range(mech.n_reactions):
-        dep = dependence_set(mech, i)
+        dep = dependence_set(mech, i, form)
         for k in range(ns - 1):
             if nu[k, i] != 0:
                 for j in dep:
@@ -469,9 +501,9 @@ def sparsity_pattern(mech):
     return mask
 
 
-def csr_pattern(mech):
+def csr_pattern(mech, form=EXACT):
     """(row_ptr [N+1], col_idx [nnz]) with columns ascending in each row."""
-    mask = sparsity_pattern(mech)
+    mask = sparsity_pattern(mech, form)
     N = mask.shape[0]
     row_ptr = np.zeros(N + 1, dtype=np.int32)
     cols = []
@@ -482,9 +514,9 @@ def csr_pattern(mech):
     return row_ptr, np.array(cols, dtype=np.int32)
 
 
-def csc_pattern(mech):
+def csc_pattern(mech, form=EXACT):
     """(col_ptr [N+1], row_idx [nnz]) with rows ascending in each column."""
-    mask = sparsity_pattern(mech)
+    mask = sparsity_pattern(mech, form)
     N = mask.shape[0]
     col_ptr = np.zeros(N + 1, dtype=np.int32)
     rows = []
@@ -495,14 +527,14 @@ def csc_pattern(mech):
     return col_ptr, np.array(rows, dtype=np.int32)
 
 
-def dense_to_csr_values(mech, J):
+def dense_to_csr_values(mech, J, form=EXACT):
     """Values [nnz, n] of a dense Jacobian stack in CSR order."""
-    row_ptr, col = csr_pattern(mech)
+    row_ptr, col = csr_pattern(mech, form)
     rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
     return J[rows, col]
 
 
-def dense_to_csc_values(mech, J):
-    col_ptr, row = csc_pattern(mech)
+def dense_to_csc_values(mech, J, form=EXACT):
+    col_ptr, row = csc_pattern(mech, form)
     cols = np.repeat(np.arange(len(col_ptr) - 1), np.diff(col_ptr))
     return J[row, cols]

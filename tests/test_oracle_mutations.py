@@ -110,12 +110,42 @@ def pin_troe_center(K):
     return bool(abs(F - Fc) <= 1e-12 * Fc)
 
 
+def pin_approx(K):
+    """Approximate Jacobian (Sec. 3.4): derivatives worked by hand for
+    H + H + M -> H2 + M with alpha_N2 = 2, alpha_H2O = 3 (bath gas counted at
+    unit efficiency), and pattern superset + tightness on a mechanism whose
+    bath gas has non-unit efficiencies."""
+    m = tm.single(dict(reac=[(tm.H, 2)], prod=[(tm.H2, 1)], A=1.5e12, beta=-1.1, Ea=0.0, rev=False,
+                       kind=synth.THIRD_BODY, eff={tm.N2: 2.0, tm.H2O: 3.0}))
+    phi, par = synth.make_states(m, 3, 3, 0)
+    Ja = K.jacobian(m, 0, phi, par, form=K.APPROX)
+    T, V, P = phi[0], phi[1], par
+    C = np.concatenate([phi[2:] / V, (P / (8314.46261815324 * T) - (phi[2:] / V).sum(axis=0))[None]])
+    alpha = np.ones(10)
+    alpha[tm.N2], alpha[tm.H2O] = 2.0, 3.0
+    kf = 1.5e12 * T ** -1.1
+    ok = True
+    for j in range(9):
+        want = -2.0 * kf * (2 * C[tm.H] * (j == tm.H) * (alpha @ C) + C[tm.H] ** 2 * (alpha[j] - 1.0))
+        ok &= bool(np.allclose(Ja[2 + tm.H, 2 + j], want, rtol=1e-10, atol=1e-300))
+    b = tm.bath_efficiency()
+    pa = K.sparsity_pattern(b, K.APPROX)
+    phi, par = synth.make_states(b, 12, 4, 0)
+    nz = np.any(K.jacobian(b, 0, phi, par, form=K.APPROX) != 0, axis=2)
+    forced = np.zeros_like(pa)
+    forced[:2, :] = forced[:, :2] = True
+    forced[np.arange(11), np.arange(11)] = True
+    ok &= not np.any(nz & ~pa) and bool(np.all(nz[pa & ~forced]))
+    return bool(ok)
+
+
 def all_pins(K, mechs):
     g = mechs("h2co13")
     a = tm.all_kinds()
     return dict(equilibrium=pin_equilibrium(K, g), thermo=pin_thermo(K, g),
                 cons_conp=pin_conservation(K, a, 0), cons_conv=pin_conservation(K, a, 1),
-                single=pin_single_rate(K), third_body=pin_third_body(K), troe=pin_troe_center(K))
+                single=pin_single_rate(K), third_body=pin_third_body(K), troe=pin_troe_center(K),
+                approx=pin_approx(K))
 
 
 MUTATIONS = [
@@ -133,6 +163,11 @@ MUTATIONS = [
     ("c = -0.4 - 0.67 * lF", "c = -0.4 - 0.76 * lF"),
     ("f[1] = V * Tdot / T + (R * T * V / P) * Om", "f[1] = V * Tdot / T + (R * V / P) * Om"),
     ("f[1] = P * Tdot / T + R * T * Om", "f[1] = P * Tdot / T + R * Om"),
+    # approximate Jacobian (Sec. 3.4)
+    ("                M = M + (C[ns - 1] - Cr[ns - 1])", "                M = M"),
+    ("        Cr[-1] = _re(C[-1])", "        Cr = _re(C)"),
+    ("ref = 1.0 if form == APPROX else a[bath]", "ref = a[bath]"),
+    ("    if dense and form != APPROX:", "    if dense:"),
 ]
 
 

@@ -428,7 +428,13 @@ def main():
             h, mode, pj.PJ_CSC, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
         variants["jacobian_csr_conv"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
             h, synth.CONV, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
-        del vals
+        ha = h.with_jacobian_form(pj.PJ_JAC_APPROX)
+        wba = ha.workspace_size(pj.PJ_OP_JACOBIAN, n)
+        worka = torch.empty(max(wba, 1), dtype=torch.uint8, device=dev)
+        variants["jacobian_csr_conp_approx"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
+            ha, mode, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, worka, wba, stream)) * 1e-3)
+        variants["approx_nnz"] = ha.nnz
+        del vals, worka
         torch.cuda.empty_cache()
         jd = torch.empty((N1 * N1, n), dtype=torch.float64, device=dev)
         variants["jacobian_dense_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_dense(

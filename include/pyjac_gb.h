@@ -146,12 +146,35 @@ int pj_mech_free(pj_mech* mech);
 /* Sizes: species, reactions, and nonzeros of the sparse Jacobian. */
 int pj_mech_info(const pj_mech* mech, int32_t* n_species, int32_t* n_reactions, int32_t* nnz);
 
-/* Sparsity pattern of the exact Jacobian (Sec. 3.3), identical for CONP and
+/* Jacobian forms (Sec. 3.4, "Sparsity patterns").  PJ_JAC_EXACT is the
+ * derivative of the source terms.  PJ_JAC_APPROX leaves out, in the species
+ * columns, the derivatives that reach a rate of progress through the bath
+ * gas's concentration (C_Ns = C_tot - sum_k C_k depends on every n_j) and the
+ * part of d[M]/dn_j that a non-unit bath-gas third-body efficiency spreads
+ * over every species (the bath gas is counted at unit efficiency there); the
+ * temperature and state columns, and the source terms, are unchanged.  Those
+ * derivatives are what make whole species rows dense, so the approximate
+ * pattern is sparser. */
+#define PJ_JAC_EXACT 0
+#define PJ_JAC_APPROX 1
+
+/* New handle for the same mechanism data whose Jacobian entry points (sparse,
+ * dense, Newton matrix, allocation-free, plans) and pj_sparsity / nnz use
+ * `form`.  Source terms and the VJP (always the exact derivative) do not
+ * depend on it.  Release *out with pj_mech_free().  Errors: PJ_ERR_ARG (null,
+ * unknown form), PJ_ERR_CUDA / PJ_ERR_NOMEM (upload). */
+int pj_mech_with_jacobian_form(const pj_mech* mech, int form, pj_mech** out);
+
+/* The Jacobian form of a handle (PJ_JAC_EXACT for pj_mech_create/load). */
+int pj_mech_jacobian_form(const pj_mech* mech, int32_t* form);
+
+/* Sparsity pattern of the Jacobian (Sec. 3.3), identical for CONP and
  * CONV: rows/columns of T and S dense, diagonal kept, species row k has
  * column j when a reaction that changes k has a rate depending on j (its
  * reactants, its products if reversible, species whose third-body efficiency
  * differs from the bath gas's, or every species when the bath gas takes part
- * in the rate).  fmt = PJ_CSR: h_ptr[Ns+2] row pointers, h_idx[nnz] column
+ * in the rate; for PJ_JAC_APPROX handles, efficiencies differing from 1 and
+ * no every-species clause).  fmt = PJ_CSR: h_ptr[Ns+2] row pointers, h_idx[nnz] column
  * indices ascending per row; PJ_CSC: column pointers / row indices. */
 int pj_sparsity(const pj_mech* mech, int fmt, int32_t* h_ptr, int32_t* h_idx);
 

@@ -15,6 +15,7 @@ PJ_CONP, PJ_CONV = 0, 1
 PJ_CSR, PJ_CSC, PJ_DENSE = 0, 1, 2
 PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y = 0, 1, 2, 3, 4
 PJ_MAX_SP = 4
+PJ_JAC_EXACT, PJ_JAC_APPROX = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -44,6 +45,8 @@ SIGNATURES = {
     "pj_mech_free": (C.c_int, [_vp]),
     "pj_mech_info": (C.c_int, [_vp, _ip, _ip, _ip]),
     "pj_sparsity": (C.c_int, [_vp, C.c_int, _ip, _ip]),
+    "pj_mech_with_jacobian_form": (C.c_int, [_vp, C.c_int, C.POINTER(_vp)]),
+    "pj_mech_jacobian_form": (C.c_int, [_vp, _ip]),
     "pj_eval_source_terms": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp,
                                        _vp, C.c_size_t, _vp]),
     "pj_eval_jacobian_sparse": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native as N
 from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
-                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_MAX_SP, check)
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
 
 
 def _ptr(t):
@@ -55,6 +55,19 @@ class Mechanism:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def jacobian_form(self):
+        f = C.c_int32()
+        check(N.load().pj_mech_jacobian_form(self._h, C.byref(f)), "pj_mech_jacobian_form")
+        return f.value
+
+    def with_jacobian_form(self, form) -> "Mechanism":
+        """The same mechanism with the exact (PJ_JAC_EXACT) or approximate
+        (PJ_JAC_APPROX, Sec. 3.4) Jacobian and its pattern."""
+        h = C.c_void_p()
+        check(N.load().pj_mech_with_jacobian_form(self._h, form, C.byref(h)), "pj_mech_with_jacobian_form")
+        return Mechanism(h, self.name)
 
     def sparsity(self, fmt=PJ_CSR):
         ptr = np.zeros(self.n_species + 2, dtype=np.int32)
@@ -109,6 +122,14 @@ def pj_mech_load(path: str) -> Mechanism:
     h = C.c_void_p()
     check(N.load().pj_mech_load(path.encode(), C.byref(h)), "pj_mech_load")
     return Mechanism(h, path)
+
+
+def pj_mech_with_jacobian_form(mech: Mechanism, form) -> Mechanism:
+    return mech.with_jacobian_form(form)
+
+
+def pj_mech_jacobian_form(mech: Mechanism):
+    return mech.jacobian_form
 
 
 def pj_sparsity(mech: Mechanism, fmt=PJ_CSR):

@@ -49,7 +49,11 @@ static std::vector<double> alpha_of(const pj_mech* m, int i) {
 
 // Species (< Ns-1) on which reaction i's rate depends, and whether that is
 // every species (bath gas in the rate, or a non-unit bath-gas efficiency).
+// The approximate form (Sec. 3.4) leaves out exactly those every-species
+// derivatives: efficiencies then count against the default 1, and the result
+// is never dense, so the kernels skip the bath-gas term of the reaction.
 static bool rate_dependence(const pj_mech* m, int i, std::vector<char>& dep) {
+  const bool approx = m->jac_form == PJ_JAC_APPROX;
   const int ns = m->ns, bath = ns - 1;
   dep.assign(ns - 1, 0);
   bool dense = false;
@@ -62,10 +66,12 @@ static bool rate_dependence(const pj_mech* m, int i, std::vector<char>& dep) {
     for (int a = 0; a < PJ_MAX_SP; a++) member(m->prod_sp[i * PJ_MAX_SP + a]);
   if (m->kind[i] != PJ_ELEMENTARY) {
     std::vector<double> al = alpha_of(m, i);
+    const double ref = approx ? 1.0 : al[bath];
     for (int k = 0; k < ns - 1; k++)
-      if (al[k] != al[bath]) dep[k] = 1;
+      if (al[k] != ref) dep[k] = 1;
     if (al[bath] != 1.0) dense = true;
   }
+  if (approx) return false;
   if (dense) std::fill(dep.begin(), dep.end(), 1);
   return dense;
 }
@@ -270,6 +276,37 @@ int mech_build(pj_mech* m) {
     r.dense = rate_dependence(m, i, dep) ? 1 : 0;
   }
 
+  // Every entry the Jacobian kernels accumulate into must be in the pattern
+  // (the index maps hold -1 elsewhere): for each row a reaction changes, the
+  // T and S columns, the columns of its reactants, reversible products and
+  // non-unit efficiencies, and every species column when it is dense; rows T
+  // and S and the diagonal in full.
+  {
+    auto in = [&](int i, int j) {
+      return m->pos_csr[(size_t)i * N + j] >= 0 && m->pos_csc[(size_t)i * N + j] >= 0;
+    };
+    bool ok = true;
+    for (int j = 0; j < N; j++) ok = ok && in(0, j) && in(1, j) && in(j, j);
+    std::vector<int> cols;
+    for (int q = 0; q < nr && ok; q++) {
+      const Rxn& r = rx[q];
+      cols.clear();
+      for (int a = 0; a < r.nreac; a++) cols.push_back(r.sp[a]);
+      if (r.rev)
+        for (int a = 0; a < r.nprod; a++) cols.push_back(r.sp[PJ_MAX_SP + a]);
+      for (int e = r.eff_lo; e < r.eff_hi; e++) cols.push_back(eff_sp[e]);
+      if (r.dense)
+        for (int j = 0; j < bath; j++) cols.push_back(j);
+      for (int q2 = r.row_lo; q2 < r.row_hi && ok; q2++) {
+        const int k = rows[q2].k;
+        ok = ok && in(k + 2, 0) && in(k + 2, 1);
+        for (int j : cols)
+          if (j != bath) ok = ok && in(k + 2, j + 2);
+      }
+    }
+    if (!ok) return fail(PJ_ERR_MECH, "internal: the sparsity pattern misses an entry the Jacobian kernel writes");
+  }
+
   // one device allocation holding every constant array
   const size_t o_nasa = 0;
   const size_t o_wfac = align256(o_nasa + nasa.size() * sizeof(double));
@@ -429,6 +466,59 @@ extern "C" int pj_mech_info(const pj_mech* m, int32_t* ns, int32_t* nr, int32_t*
   if (ns) *ns = m->ns;
   if (nr) *nr = m->nr;
   if (nnz) *nnz = m->nnz;
+  return PJ_OK;
+}
+
+extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech** out) {
+  if (!src || !out) return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: null argument");
+  *out = nullptr;
+  if (form != PJ_JAC_EXACT && form != PJ_JAC_APPROX)
+    return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: form must be PJ_JAC_EXACT or PJ_JAC_APPROX");
+  pj_mech* m = new (std::nothrow) pj_mech();
+  if (!m) return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
+  try {
+    m->ns = src->ns;
+    m->nr = src->nr;
+    m->W = src->W;
+    m->T_mid = src->T_mid;
+    m->nasa_low = src->nasa_low;
+    m->nasa_high = src->nasa_high;
+    m->A = src->A;
+    m->beta = src->beta;
+    m->Ea = src->Ea;
+    m->A0 = src->A0;
+    m->beta0 = src->beta0;
+    m->Ea0 = src->Ea0;
+    m->troe = src->troe;
+    m->sri = src->sri;
+    m->eff_val = src->eff_val;
+    m->kind = src->kind;
+    m->rev = src->rev;
+    m->reac_sp = src->reac_sp;
+    m->reac_nu = src->reac_nu;
+    m->prod_sp = src->prod_sp;
+    m->prod_nu = src->prod_nu;
+    m->troe_n = src->troe_n;
+    m->eff_ptr = src->eff_ptr;
+    m->eff_sp = src->eff_sp;
+  } catch (...) {
+    delete m;
+    return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
+  }
+  m->jac_form = form;
+  int rc = mech_build(m);
+  if (rc) {
+    mech_release(m);
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return PJ_OK;
+}
+
+extern "C" int pj_mech_jacobian_form(const pj_mech* m, int32_t* form) {
+  if (!m || !form) return fail(PJ_ERR_ARG, "pj_mech_jacobian_form: null argument");
+  *form = m->jac_form;
   return PJ_OK;
 }
 

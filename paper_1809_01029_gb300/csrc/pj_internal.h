@@ -82,6 +82,7 @@ struct DevMech {
 
 struct pj_mech {
   int32_t ns = 0, nr = 0, nnz = 0;
+  int32_t jac_form = PJ_JAC_EXACT;  // Jacobian form of the pattern and kernels
   int device = -1;
   // host copies of the description
   std::vector<double> W, T_mid, nasa_low, nasa_high, A, beta, Ea, A0, beta0, Ea0, troe, sri, eff_val;

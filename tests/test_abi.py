@@ -137,3 +137,27 @@ def test_no_device_means_no_silent_fallback(lib):
     p = C.c_void_p(16)
     rc = lib.pj_eval_source_terms(h.handle, 0, 1, p, p, 1, p, None, None, 0, None)
     assert rc == N.PJ_ERR_CUDA
+
+
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "h2co13", "gri53", "usc111", "ic5874"])
+def test_approximate_pattern_bit_exact_against_oracle(lib, mechs, name):
+    """The approximate Jacobian form (Sec. 3.4) has its own, sparser pattern."""
+    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency") else mechs(name)
+    h = pj.pj_mech_create(m)
+    ha = h.with_jacobian_form(pj.PJ_JAC_APPROX)
+    assert (h.jacobian_form, ha.jacobian_form) == (pj.PJ_JAC_EXACT, pj.PJ_JAC_APPROX)
+    assert ha.nnz == int(oracle.sparsity_pattern(m, oracle.APPROX).sum()) <= h.nnz
+    for fmt, ref in ((pj.PJ_CSR, oracle.csr_pattern(m, oracle.APPROX)),
+                     (pj.PJ_CSC, oracle.csc_pattern(m, oracle.APPROX))):
+        ptr, idx = ha.sparsity(fmt)
+        assert ptr.tobytes() == ref[0].astype(np.int32).tobytes()
+        assert idx.tobytes() == ref[1].astype(np.int32).tobytes()
+    back = ha.with_jacobian_form(pj.PJ_JAC_EXACT)
+    assert back.nnz == h.nnz and np.array_equal(back.sparsity(pj.PJ_CSR)[1], h.sparsity(pj.PJ_CSR)[1])
+
+
+def test_jacobian_form_rejects_unknown_form(lib, mechs):
+    h = pj.pj_mech_create(mechs("h2co13"))
+    out = C.c_void_p()
+    assert lib.pj_mech_with_jacobian_form(h.handle, 7, C.byref(out)) == N.PJ_ERR_ARG
+    assert lib.pj_mech_with_jacobian_form(None, 0, C.byref(out)) == N.PJ_ERR_ARG

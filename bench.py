@@ -207,7 +207,22 @@ def other_workloads(pj, synth, torch, dev, stream):
     t = _time(torch, stream, lambda: pj.pj_vjp(h, synth.CONP, n, par, phi, n, uw, uT, y, g, gt, None, w, wb, stream),
               reps=10)
     out["gri53_64k_vjp"] = n / (t * 1e-3)
-    del y, g, gt, w, phi, par, uw, uT
+    del y, g, gt, w, uw, uT
+    # same states: analytical vs first-order finite-difference CSR Jacobian
+    # (the paper's speedup comparison)
+    f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    J = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    wb = h.workspace_size(pj.PJ_OP_JACOBIAN, n)
+    w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    ta = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f,
+                                                                 None, w, wb, stream), reps=10)
+    wb = h.workspace_size(pj.PJ_OP_FD, n)
+    w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    tf = _time(torch, stream, lambda: pj.pj_eval_jacobian_fd(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f,
+                                                             None, w, wb, stream), reps=2)
+    out["gri53_64k_fd_jacobian_csr"] = n / (tf * 1e-3)
+    out["gri53_64k_analytical_over_fd"] = tf / ta
+    del J, f, w, phi, par
     torch.cuda.empty_cache()
     out.update(ragged_workload(pj, synth, torch, dev, stream))
     return out

@@ -60,7 +60,7 @@ extern "C" {
 #define PJ_CONP 0
 #define PJ_CONV 1
 
-/* Jacobian storage (Sec. 3.3: compressed row / column storage) */
+/* Jacobian storage (Sec. 3.4: compressed row / column storage) */
 #define PJ_CSR 0
 #define PJ_CSC 1
 #define PJ_DENSE 2
@@ -128,7 +128,7 @@ const char* pj_last_error(void);
 const char* pj_version(void);
 
 /* Build a mechanism from arrays (copied), pack its constants for the
- * kernels, build the fixed sparsity pattern (Sec. 3.3) and upload both to the
+ * kernels, build the fixed sparsity pattern (Sec. 3.4) and upload both to the
  * current device.  *out receives a handle to release with pj_mech_free().
  * With no CUDA device present the handle is host-only: pj_mech_info and
  * pj_sparsity work, evaluation calls return PJ_ERR_CUDA.
@@ -168,7 +168,7 @@ int pj_mech_with_jacobian_form(const pj_mech* mech, int form, pj_mech** out);
 /* The Jacobian form of a handle (PJ_JAC_EXACT for pj_mech_create/load). */
 int pj_mech_jacobian_form(const pj_mech* mech, int32_t* form);
 
-/* Sparsity pattern of the Jacobian (Sec. 3.3), identical for CONP and
+/* Sparsity pattern of the Jacobian (Sec. 3.4), identical for CONP and
  * CONV: rows/columns of T and S dense, diagonal kept, species row k has
  * column j when a reaction that changes k has a rate depending on j (its
  * reactants, its products if reversible, species whose third-body efficiency
@@ -189,7 +189,7 @@ int pj_eval_source_terms(const pj_mech* mech, int mode, int64_t n, const double*
                          void* d_work, size_t work_bytes, void* stream);
 
 /* Exact analytical Jacobian J_ij = d f_i / d Phi_j (Sec. 2.2 "Jacobian
- * arrangement"; sparse storage Sec. 3.3) in CSR (fmt = PJ_CSR) or CSC
+ * arrangement"; sparse storage Sec. 3.4) in CSR (fmt = PJ_CSR) or CSC
  * (PJ_CSC) value order: d_vals[e*ld + s].  d_dphi (required, same layout as
  * d_phi) receives the source terms, which the Jacobian kernel computes on the
  * way.  d_work must point to pj_workspace_size(PJ_OP_JACOBIAN) bytes of
@@ -206,7 +206,7 @@ int pj_eval_jacobian_dense(const pj_mech* mech, int mode, int64_t n, const doubl
 
 /* Newton-iteration matrix M = I - h*gamma*J in FP32 (the matrix an implicit
  * integrator factors; the paper motivates the Jacobian by implicit
- * integration, Sec. 1, Sec. 3.3).  Rates, Gibbs-energy differences and
+ * integration, Sec. 1, Sec. 3.4).  Rates, Gibbs-energy differences and
  * equilibrium constants, every exponential and the source terms are FP64;
  * the derivative arithmetic, the accumulation of J and the assembly of M are
  * FP32.  d_h[n] is the per-state step h (device), gamma a scalar; fmt is
@@ -243,11 +243,26 @@ int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int6
 #define PJ_OP_NEWTON 2
 #define PJ_OP_VJP 3
 #define PJ_OP_Y 4
+#define PJ_OP_FD 5
 
 /* Device scratch (bytes) an operation needs for a batch of n states; 0 when
  * the per-state working arrays fit in shared memory (PJ_OP_VJP always needs
  * room for its per-warp parameter-gradient partial sums). */
 int pj_workspace_size(const pj_mech* mech, int op, int64_t n, size_t* bytes);
+
+/* First-order forward finite-difference Jacobian, the comparator of
+ * Sec. 3.5.2 (the analytical Jacobian's speedup over it): column j is
+ * (f(Phi + h_j e_j) - f(Phi)) / h_j with delta_j = 2^-26 max(|Phi_j|,
+ * 2^-26 n_tot), n_tot = P V / (R T), and h_j = (Phi_j + delta_j) - Phi_j
+ * (the paper gives no step rule).  Same layout and formats as the
+ * analytical entry points (fmt = PJ_CSR / PJ_CSC values in the handle's
+ * pattern, PJ_DENSE rows); d_dphi (required) receives f(Phi).  Costs N + 1
+ * source-term evaluations per state.  Workspace: pj_workspace_size(PJ_OP_FD)
+ * bytes, always nonzero.  A column whose perturbed state is invalid is NaN
+ * without counting in *d_status (the state itself is validated as usual). */
+int pj_eval_jacobian_fd(const pj_mech* mech, int mode, int fmt, int64_t n, const double* d_param,
+                        const double* d_phi, int64_t ld, double* d_vals, double* d_dphi, int* d_status,
+                        void* d_work, size_t work_bytes, void* stream);
 
 /* Forward values of the differentiation form: y = (wdot_0 .. wdot_{Ns-1},
  * dT/dt) per state, the species production rates of Sec. 2.2 (bath gas

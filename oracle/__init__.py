@@ -9,4 +9,4 @@ from .kinetics import (CONP, CONV, EXACT, APPROX, R, R_CAL, P_ATM, concentration
                        source_terms_from_rates, jacobian, jacobian_columns, source_term_envelope, jacobian_envelope,
                        sparsity_pattern, csr_pattern, csc_pattern, dense_to_csr_values,
                        dense_to_csc_values, net_stoich, dependence_set)
-from .forms import newton_matrix, vjp, outputs_y, y_jacobian, vjp_envelope
+from .forms import newton_matrix, vjp, outputs_y, y_jacobian, vjp_envelope, fd_jacobian, fd_steps

@@ -5,17 +5,22 @@ TEST INFRASTRUCTURE ONLY (same rules as ``oracle.kinetics``).
 
 * Newton matrix M = I - h gamma J (the matrix an implicit integrator factors;
   the paper motivates the Jacobian by implicit integration, Sec. 1 and
-  Sec. 3.3), here in float64.
+  Sec. 3.4), here in float64.
 * VJP of y = (wdot_0 .. wdot_{Ns-1}, dT/dt): g_Phi = (dy/dPhi)^T u per state
   and g_theta = sum over states of (dy/dtheta)^T u for the per-reaction
   parameters theta_i = (ln A_i, beta_i, Ea_i) of the high-pressure (or only)
   Arrhenius set, all by complex-step differentiation.
+* First-order forward finite-difference Jacobian, the comparator of
+  Sec. 3.5.2 (the analytical Jacobian's speedup over it): column j is
+  (f(Phi + h_j e_j) - f(Phi)) / h_j.  The paper gives no step rule; this one
+  uses delta_j = 2^-26 max(|Phi_j|, 2^-26 n_tot), n_tot = P V / (R T), and
+  the realised step h_j = (Phi_j + delta_j) - Phi_j.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .kinetics import CONP, R, rates, source_terms_from_rates, jacobian, _cs_step
+from .kinetics import CONP, R, rates, source_terms, source_terms_from_rates, jacobian, _cs_step
 
 
 def newton_matrix(mech, mode, phi, param, h, gamma=1.0):
@@ -95,3 +100,33 @@ def vjp(mech, mode, phi, param, u_wdot, u_T):
     # so one complex evaluation per parameter kind gives d q_i / d theta_i for
     # every i at once; y is then linear in q.
     return g_phi, _theta_terms(mech, mode, phi, param, u_wdot, u_T)
+
+
+FD_SCALE = 2.0 ** -26        # about sqrt(unit roundoff); a power of two, so scaling is exact
+
+
+def fd_steps(mech, mode, phi, param):
+    """Realised forward-difference steps h [N, n] of fd_jacobian."""
+    T = phi[0]
+    V, P = (phi[1], param) if mode == CONP else (param, phi[1])
+    ntot = (P * V) / (R * T)
+    h = np.empty_like(phi)
+    for j in range(phi.shape[0]):
+        d = FD_SCALE * np.maximum(np.abs(phi[j]), FD_SCALE * ntot)
+        h[j] = (phi[j] + d) - phi[j]
+    return h
+
+
+def fd_jacobian(mech, mode, phi, param):
+    """Dense first-order forward finite-difference Jacobian [N, N, n] and the
+    source terms at Phi (Sec. 3.5.2's comparator; step rule in the module
+    notes)."""
+    N = phi.shape[0]
+    f0 = source_terms(mech, mode, phi, param)
+    h = fd_steps(mech, mode, phi, param)
+    J = np.empty((N, N, phi.shape[1]))
+    for j in range(N):
+        x = phi.copy()
+        x[j] = phi[j] + h[j]
+        J[:, j] = (source_terms(mech, mode, x, param) - f0) / h[j]
+    return J, f0

@@ -447,7 +447,7 @@ def jacobian_envelope(mech, mode, phi, param):
 
 
 # ---------------------------------------------------------------------------
-# sparsity pattern (Sec. 3.3)
+# sparsity pattern (Sec. 3.4)
 # ---------------------------------------------------------------------------
 def dependence_set(mech, i, form=EXACT):
     """Species j < Ns-1 on which the rate of progress of reaction i depends.
@@ -455,7 +455,7 @@ def dependence_set(mech, i, form=EXACT):
     Reactants; products if reversible; for third-body / falloff reactions the
     species whose efficiency differs from the bath gas's; and every species
     when the bath gas takes part in the rate (as a reactant, as a product of a
-    reversible reaction) or has a non-unit efficiency (Sec. 3.3).
+    reversible reaction) or has a non-unit efficiency (Sec. 3.4).
     For the approximate form (Sec. 3.4) the last clause is dropped and the
     efficiencies are compared with the default 1 instead of the bath gas's.
     """
@@ -483,7 +483,7 @@ def sparsity_pattern(mech, form=EXACT):
 
     Rows/columns 0 (T) and 1 (V or P) are dense and the diagonal is kept; a
     species row k has column j when some reaction changes k (nu_ki != 0) and
-    its rate depends on j (Sec. 3.3; for form=APPROX the dependence of
+    its rate depends on j (Sec. 3.4; for form=APPROX the dependence of
     Sec. 3.4's approximate form).  Identical for CONP and CONV.
     """
     ns, N = mech.n_species, mech.n_species + 1

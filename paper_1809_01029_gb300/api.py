@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native as N
 from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
-                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
 
 
 def _ptr(t):
@@ -155,6 +155,14 @@ def pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, vals, dphi=None,
                  "pj_eval_jacobian_sparse")
 
 
+def pj_eval_jacobian_fd(mech, mode, fmt, n, param, phi, ld, vals, dphi=None, status=None, work=None,
+                        work_bytes=0, stream=None):
+    return check(N.load().pj_eval_jacobian_fd(mech.handle, mode, fmt, n, _ptr(param), _ptr(phi), ld,
+                                               _ptr(vals), _ptr(dphi), _ptr(status), _ptr(work),
+                                               work_bytes, _stream(stream)),
+                 "pj_eval_jacobian_fd")
+
+
 def pj_eval_jacobian_dense(mech, mode, n, param, phi, ld, jac, dphi=None, status=None, work=None,
                            work_bytes=0, stream=None):
     return check(N.load().pj_eval_jacobian_dense(mech.handle, mode, n, _ptr(param), _ptr(phi), ld, _ptr(jac),
@@ -243,6 +251,22 @@ def jacobian_sparse(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, sta
         dphi = _dphi_like(mech, phi, ld, n)
     work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
     pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, out, dphi, status, work, wb, stream)
+    return out
+
+
+def jacobian_fd(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=None, stream=None):
+    """First-order forward finite-difference Jacobian (the comparator), in
+    the layout of jacobian_sparse (fmt CSR/CSC) or jacobian_dense (PJ_DENSE)."""
+    import torch
+    n, ld = _check_batch(mech, phi, param)
+    N1 = mech.n_species + 1
+    if out is None:
+        rows = N1 * N1 if fmt == PJ_DENSE else mech.nnz
+        out = torch.empty((rows, ld), dtype=torch.float64, device=phi.device)[:, :n]
+    if dphi is None:
+        dphi = _dphi_like(mech, phi, ld, n)
+    work, wb = _workspace(mech, PJ_OP_FD, n, phi.device)
+    pj_eval_jacobian_fd(mech, mode, fmt, n, param, phi, ld, out, dphi, status, work, wb, stream)
     return out
 
 

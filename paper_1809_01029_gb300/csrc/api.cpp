@@ -39,6 +39,7 @@ extern "C" int pj_workspace_size(const pj_mech* m, int op, int64_t n, size_t* by
     case PJ_OP_NEWTON: *bytes = workspace_bytes(jacobian_arrays(), m->ns, n); return PJ_OK;
     case PJ_OP_VJP:
     case PJ_OP_Y: *bytes = form_workspace_bytes(op, m->dm, n); return PJ_OK;
+    case PJ_OP_FD: *bytes = fd_workspace_bytes(m->ns, n); return PJ_OK;
     default: return fail(PJ_ERR_ARG, "pj_workspace_size: unknown op");
   }
 }
@@ -62,6 +63,19 @@ extern "C" int pj_eval_jacobian_sparse(const pj_mech* m, int mode, int fmt, int6
   if (n == 0) return PJ_OK;
   return launch_jacobian(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, work, work_bytes,
                          (cudaStream_t)stream);
+}
+
+extern "C" int pj_eval_jacobian_fd(const pj_mech* m, int mode, int fmt, int64_t n, const double* param,
+                                   const double* phi, int64_t ld, double* vals, double* dphi, int* status,
+                                   void* work, size_t work_bytes, void* stream) {
+  if (fmt != PJ_CSR && fmt != PJ_CSC && fmt != PJ_DENSE)
+    return fail(PJ_ERR_ARG, "pj_eval_jacobian_fd: fmt must be PJ_CSR, PJ_CSC or PJ_DENSE");
+  int rc = check_common("pj_eval_jacobian_fd", m, mode, n, ld, param, phi, vals);
+  if (rc) return rc;
+  if (n > 0 && !dphi) return fail(PJ_ERR_ARG, "pj_eval_jacobian_fd: d_dphi is required");
+  if (n == 0) return PJ_OK;
+  return launch_fd_jacobian(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, work, work_bytes,
+                            (cudaStream_t)stream);
 }
 
 extern "C" int pj_eval_jacobian_dense(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi,

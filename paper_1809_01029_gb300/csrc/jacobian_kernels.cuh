@@ -1,4 +1,4 @@
-// The analytical Jacobian kernels (Sec. 2.2, assembled as in Sec. 3.3):
+// The analytical Jacobian kernels (Sec. 2.2, assembled as in Sec. 3.4):
 // k_jacobian keeps each state's C_k, g_k/RT and h_k/RT in shared memory or a
 // global workspace; k_jacobian_tm keeps h_k/RT in tensor memory.  Both call
 // jacobian_state for one state per thread.  Included by jacobian_inst.cu,

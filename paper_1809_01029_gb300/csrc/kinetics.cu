@@ -20,7 +20,7 @@
 //    the SM and no FP64 add on the SM); each entry is owned by one thread,
 //    whose reductions apply in program order, so results are deterministic.
 //    Targets come from a static full -> sparse index map built at mechanism
-//    load (the mapping Sec. 3.3 proposes instead of a per-entry search).
+//    load (the mapping Sec. 3.4 proposes instead of a per-entry search).
 //  * This file holds the source-term kernel and the launch planning; the
 //    Jacobian kernels are in jacobian_kernels.cuh (instantiated by
 //    jacobian_inst.cu).

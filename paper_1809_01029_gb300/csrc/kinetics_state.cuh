@@ -122,7 +122,7 @@ __device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
   return DT(nud) * x;
 }
 
-// Analytical Jacobian (Sec. 2.2, Sec. 3.3).  Rates, equilibrium constants,
+// Analytical Jacobian (Sec. 2.2, Sec. 3.4).  Rates, equilibrium constants,
 // exponentials and source terms are always FP64.  DT is the type of the
 // derivative arithmetic, the entry accumulation and the output: double for
 // J itself, float for the Newton-matrix form.  With NEWTON the final pass

@@ -64,6 +64,10 @@ int launch_newton_f32(const DevMech& m, int mode, int fmt, int64_t n, const doub
 int launch_jacobian_on_scratch(const DevMech& m, int mode, int fmt, int64_t n, const double* param,
                                const double* phi, int64_t ld, double* J, double* dphi, int* status,
                                double* scratch, int64_t scratch_threads, cudaStream_t st);
+int launch_fd_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,
+                       int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
+                       cudaStream_t st);
+size_t fd_workspace_bytes(int ns, int64_t n);
 int launch_diag_exp(const DevMech& m, int64_t n, const double* x, double* y_ours, double* y_lib, cudaStream_t st);
 int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
                   double* y, int* status, void* work, size_t work_bytes, cudaStream_t st);

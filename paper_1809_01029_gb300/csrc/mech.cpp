@@ -1,7 +1,7 @@
 // Host side of libpyjac_gb: mechanism validation, packing of the kernel
-// constants, the fixed sparsity pattern of the exact Jacobian (Sec. 3.3) and
+// constants, the fixed sparsity pattern of the exact Jacobian (Sec. 3.4) and
 // the static full-index -> sparse-index maps the paper proposes in place of a
-// per-entry search of the compressed row (Sec. 3.3, last paragraph).
+// per-entry search of the compressed row (Sec. 3.4, last paragraph).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -357,7 +357,7 @@ def test_pattern_superset_and_tight(mechs, mk):
 
 
 def test_bath_gas_rules_make_rows_dense():
-    """Sec. 3.3: a bath-gas reactant, or a non-unit bath-gas efficiency, fills
+    """Sec. 3.4: a bath-gas reactant, or a non-unit bath-gas efficiency, fills
     every species row the reaction changes."""
     m = tm.bath_efficiency()
     mask = K.sparsity_pattern(m)

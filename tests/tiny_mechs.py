@@ -1,5 +1,5 @@
 """Hand-built tiny mechanisms that cover every reaction kind and the bath-gas
-cases of the sparsity rules (Sec. 3.3).  Inputs only: no method arithmetic.
+cases of the sparsity rules (Sec. 3.4).  Inputs only: no method arithmetic.
 
 Species (last = bath gas N2): 0 H, 1 O, 2 H2, 3 O2, 4 OH, 5 H2O, 6 HO2, 7 N, 8 NO, 9 N2
 """

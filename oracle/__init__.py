@@ -10,3 +10,4 @@ from .kinetics import (CONP, CONV, EXACT, APPROX, R, R_CAL, P_ATM, concentration
                        sparsity_pattern, csr_pattern, csc_pattern, dense_to_csr_values,
                        dense_to_csc_values, net_stoich, dependence_set)
 from .forms import newton_matrix, vjp, outputs_y, y_jacobian, vjp_envelope, fd_jacobian, fd_steps
+from . import linalg

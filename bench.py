@@ -157,6 +157,53 @@ def _time(torch, stream, fn, reps=5):
     return a.elapsed_time(b) / reps
 
 
+def lu_workloads(pj, synth, torch, dev, stream):
+    """States/s of the Newton-matrix LU factorisation and solve: FP64 with
+    M = I - h J formed from the FP64 Jacobian (53 species), and FP32 of the
+    FP32 Newton matrix (111 species), 262,144 states each."""
+    out = {}
+    n = 262144
+    for name, prec in (("gri53", pj.PJ_F64), ("usc111", pj.PJ_F32)):
+        m = synth.make_mechanism(name)
+        h = pj.pj_mech_create(m)
+        N1 = m.n_species + 1
+        phi_h, par_h = synth.make_states(m, n, 2018 + 3, synth.CONP)
+        phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+        hs = torch.from_numpy(synth.make_step_sizes(n, 2018 + 3)).to(dev)
+        f = torch.empty((N1, n), dtype=torch.float64, device=dev)
+        lu_nnz, _ = h.lu_info()
+        dt = torch.float64 if prec == pj.PJ_F64 else torch.float32
+        vals = torch.empty((h.nnz, n), dtype=dt, device=dev)
+        if prec == pj.PJ_F64:
+            wb = h.workspace_size(pj.PJ_OP_JACOBIAN, n)
+            w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+            pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, vals, f, None, w, wb, stream)
+            hh = hs
+        else:
+            wb = h.workspace_size(pj.PJ_OP_NEWTON, n)
+            w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+            pj.pj_newton_matrix_f32(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, hs, 1.0, vals, f, None, w, wb, stream)
+            hh = None
+        del w
+        lu = torch.empty((lu_nnz, n), dtype=dt, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        wl = h.workspace_size(pj.PJ_OP_LU, n)
+        w = torch.empty(max(wl, 1), dtype=torch.uint8, device=dev)
+        reps = 3
+        t = _time(torch, stream, lambda: pj.pj_lu_factor(h, prec, n, vals, n, lu, hh, 1.0, status, w, wl, stream),
+                  reps=reps)
+        tag = f"{name}_256k_lu_{'f64' if prec == pj.PJ_F64 else 'f32'}"
+        out[f"{tag}_factor"] = n / (t * 1e-3)
+        out[f"{tag}_states_flagged"] = int(status.item()) // (reps + 1)
+        b = torch.randn((N1, n), dtype=dt, device=dev)
+        x = torch.empty_like(b)
+        t = _time(torch, stream, lambda: pj.pj_lu_solve(h, prec, n, lu, n, b, x, stream), reps=10)
+        out[f"{tag}_solve"] = n / (t * 1e-3)
+        del vals, lu, b, x, w, phi, par, hs, f
+        torch.cuda.empty_cache()
+    return out
+
+
 def other_workloads(pj, synth, torch, dev, stream):
     """States/s of the other measured cases (one launch per evaluation)."""
     out = {}
@@ -224,6 +271,7 @@ def other_workloads(pj, synth, torch, dev, stream):
     out["gri53_64k_analytical_over_fd"] = tf / ta
     del J, f, w, phi, par
     torch.cuda.empty_cache()
+    out.update(lu_workloads(pj, synth, torch, dev, stream))
     out.update(ragged_workload(pj, synth, torch, dev, stream))
     return out
 

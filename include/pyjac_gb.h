@@ -244,6 +244,7 @@ int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int6
 #define PJ_OP_VJP 3
 #define PJ_OP_Y 4
 #define PJ_OP_FD 5
+#define PJ_OP_LU 6
 
 /* Device scratch (bytes) an operation needs for a batch of n states; 0 when
  * the per-state working arrays fit in shared memory (PJ_OP_VJP always needs
@@ -342,6 +343,46 @@ int pj_plan_run(pj_plan* plan, void* stream);
  * shape drops the graph. */
 int pj_plan_capture(pj_plan* plan, void* stream);
 int pj_plan_launch(pj_plan* plan, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Linear algebra of the Newton matrix M = I - h gamma J: batched LU and solve
+ * in the Jacobian's fixed pattern (Sec. 5 names these as the missing piece
+ * for implicit integration, over many small matrices rather than one large).
+ * Per handle (and Jacobian form) a symbolic phase fixes, at creation:
+ *  - the pivot order perm: species by greedy minimum degree on the
+ *    symmetrised species block (ties by lowest index), then T and S;
+ *  - the fill of LU without pivoting of A = P M P^T (A[k][l] = M[perm[k]]
+ *    [perm[l]]): L unit lower, U upper;
+ *  - the storage order of the lu_nnz factor values per state: strictly lower
+ *    rows k = 0..N-1 (columns ascending), then upper rows k = N-1..0, each as
+ *    1/U_kk followed by U_kj, j > k ascending.
+ * No pivoting: a state whose factors are not all finite (a zero pivot, or
+ * overflow -- FP32's range is exceeded by very stiff states, whose unscaled
+ * entries reach 1e20 and more) increments *d_status once; M of an implicit
+ * step is the identity plus h gamma J.
+ * ------------------------------------------------------------------------ */
+#define PJ_F64 0
+#define PJ_F32 1
+
+/* lu_nnz and (h_perm non-NULL) perm[N]. */
+int pj_lu_info(const pj_mech* mech, int32_t* lu_nnz, int32_t* h_perm);
+
+/* Pivot-order (row, column) of each factor value, in storage order. */
+int pj_lu_pattern(const pj_mech* mech, int32_t* h_rows, int32_t* h_cols);
+
+/* Factor n matrices.  d_vals: [nnz x ld] CSR values (pj_sparsity order) of
+ * M -- or, with d_h non-NULL, of J, and M = I - d_h[s] gamma J is formed on
+ * the way in -- in double (PJ_F64) or float (PJ_F32, e.g. the output of
+ * pj_newton_matrix_f32); d_lu: [lu_nnz x ld] factors of the same type.
+ * Workspace: pj_workspace_size(PJ_OP_LU) bytes (0 unless N^2 values exceed
+ * shared memory). */
+int pj_lu_factor(const pj_mech* mech, int prec, int64_t n, const void* d_vals, int64_t ld, const double* d_h,
+                 double gamma, void* d_lu, int* d_status, void* d_work, size_t work_bytes, void* stream);
+
+/* Solve M x = b for n states with factors from pj_lu_factor: d_b, d_x
+ * [N x ld] of the factors' type (d_x may equal d_b). */
+int pj_lu_solve(const pj_mech* mech, int prec, int64_t n, const void* d_lu, int64_t ld, const void* d_b,
+                void* d_x, void* stream);
 
 #ifdef __cplusplus
 }

@@ -105,19 +105,17 @@ def newton_dense(mech, J_csr_vals, h, gamma, form=EXACT):
 
 
 def lu_factor(M, perm):
-    """Doolittle LU without pivoting of A = P M P^T for every state:
-    (L [N, N, n] unit lower, U [N, N, n] upper)."""
+    """LU without pivoting of A = P M P^T for every state by Gaussian
+    elimination: at pivot k, l_ik = a_ik / a_kk and a_ij -= l_ik a_kj for
+    i, j > k.  Returns (L [N, N, n] unit lower, U [N, N, n] upper)."""
     A = M[np.ix_(perm, perm)].astype(np.float64).copy()
     N = A.shape[0]
-    L = np.zeros_like(A)
-    U = np.zeros_like(A)
     for k in range(N):
-        L[k, k] = 1.0
-        for j in range(k, N):
-            U[k, j] = A[k, j] - sum(L[k, m] * U[m, j] for m in range(k))
-        for i in range(k + 1, N):
-            L[i, k] = (A[i, k] - sum(L[i, m] * U[m, k] for m in range(k))) / U[k, k]
-    return L, U
+        A[k + 1:, k] = A[k + 1:, k] / A[k, k]
+        A[k + 1:, k + 1:] -= A[k + 1:, k][:, None] * A[k, k + 1:][None, :]
+    eye = np.eye(N)[:, :, None]
+    low = np.tril(np.ones((N, N)), -1)[:, :, None]
+    return low * A + eye, np.triu(np.ones((N, N)))[:, :, None] * A
 
 
 def lu_values(L, U, storage):

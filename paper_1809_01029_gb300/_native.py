@@ -13,7 +13,8 @@ from . import build as _build
 PJ_OK, PJ_ERR_ARG, PJ_ERR_MECH, PJ_ERR_CUDA, PJ_ERR_NOMEM, PJ_ERR_UNSUPPORTED, PJ_ERR_TIMEOUT = range(7)
 PJ_CONP, PJ_CONV = 0, 1
 PJ_CSR, PJ_CSC, PJ_DENSE = 0, 1, 2
-PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD = 0, 1, 2, 3, 4, 5
+PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_LU = 0, 1, 2, 3, 4, 5, 6
+PJ_F64, PJ_F32 = 0, 1
 PJ_MAX_SP = 4
 PJ_JAC_EXACT, PJ_JAC_APPROX = 0, 1
 
@@ -55,6 +56,11 @@ SIGNATURES = {
                                          _vp, C.c_size_t, _vp]),
     "pj_eval_jacobian_fd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
                                       _vp, _vp, _vp, C.c_size_t, _vp]),
+    "pj_lu_info": (C.c_int, [_vp, _ip, _ip]),
+    "pj_lu_pattern": (C.c_int, [_vp, _ip, _ip]),
+    "pj_lu_factor": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, C.c_int64, _vp, C.c_double, _vp, _vp, _vp,
+                               C.c_size_t, _vp]),
+    "pj_lu_solve": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, C.c_int64, _vp, _vp, _vp]),
     "pj_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
     "pj_eval_y": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_size_t, _vp]),
     "pj_vjp": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,

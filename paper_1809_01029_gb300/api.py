@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native as N
 from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
-                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_LU, PJ_F64, PJ_F32, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
 
 
 def _ptr(t):
@@ -75,6 +75,21 @@ class Mechanism:
         check(N.load().pj_sparsity(self._h, fmt, ptr.ctypes.data_as(N._ip), idx.ctypes.data_as(N._ip)),
               "pj_sparsity")
         return ptr, idx[: self.nnz]
+
+    def lu_info(self):
+        """(lu_nnz, perm [N]) of the Newton-matrix LU."""
+        k = C.c_int32()
+        perm = np.zeros(self.n_species + 1, dtype=np.int32)
+        check(N.load().pj_lu_info(self._h, C.byref(k), perm.ctypes.data_as(N._ip)), "pj_lu_info")
+        return k.value, perm
+
+    def lu_pattern(self):
+        """Pivot-order (rows, cols) of the factor values in storage order."""
+        k, _ = self.lu_info()
+        r = np.zeros(max(k, 1), dtype=np.int32)
+        c = np.zeros(max(k, 1), dtype=np.int32)
+        check(N.load().pj_lu_pattern(self._h, r.ctypes.data_as(N._ip), c.ctypes.data_as(N._ip)), "pj_lu_pattern")
+        return r[:k], c[:k]
 
     def workspace_size(self, op, n):
         b = C.c_size_t()
@@ -429,3 +444,53 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return PJ_F64
+    if t.dtype == torch.float32:
+        return PJ_F32
+    raise TypeError("LU values must be float64 or float32")
+
+
+def pj_lu_factor(mech, prec, n, vals, ld, lu, h=None, gamma=1.0, status=None, work=None, work_bytes=0,
+                 stream=None):
+    return check(N.load().pj_lu_factor(mech.handle, prec, n, _ptr(vals), ld, _ptr(h), float(gamma), _ptr(lu),
+                                       _ptr(status), _ptr(work), work_bytes, _stream(stream)), "pj_lu_factor")
+
+
+def pj_lu_solve(mech, prec, n, lu, ld, b, x, stream=None):
+    return check(N.load().pj_lu_solve(mech.handle, prec, n, _ptr(lu), ld, _ptr(b), _ptr(x), _stream(stream)),
+                 "pj_lu_solve")
+
+
+def lu_factor(mech, vals, h=None, gamma=1.0, out=None, status=None, stream=None):
+    """Factors [lu_nnz, n] of M (vals: CSR values of M, or of J with h given:
+    M = I - h gamma J), in vals' precision."""
+    import torch
+    nnz, n = vals.shape
+    ld = vals.stride(0) if n > 0 else 1
+    if vals.stride(1) != 1 or nnz != mech.nnz:
+        raise ValueError("vals must be [nnz, n] with unit stride along states")
+    lu_nnz, _ = mech.lu_info()
+    if out is None:
+        out = torch.empty((lu_nnz, max(ld, 1)), dtype=vals.dtype, device=vals.device)[:, :n]
+    wb = mech.workspace_size(PJ_OP_LU, n)
+    work = torch.empty(wb, dtype=torch.uint8, device=vals.device) if wb else None
+    pj_lu_factor(mech, _prec(vals), n, vals, max(ld, 1), out, h, gamma, status, work, wb, stream)
+    return out
+
+
+def lu_solve(mech, lu, b, out=None, stream=None):
+    """x with M x = b per state ([N, n], lu's precision)."""
+    import torch
+    n = b.shape[1]
+    ld = lu.stride(0)
+    if b.stride(0) != ld or b.stride(1) != 1:
+        raise ValueError("b must share lu's leading dimension")
+    if out is None:
+        out = torch.empty((b.shape[0], ld), dtype=b.dtype, device=b.device)[:, :n]
+    pj_lu_solve(mech, _prec(lu), n, lu, ld, b, out, stream)
+    return out

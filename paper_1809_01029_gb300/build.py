@@ -17,7 +17,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpyjac_gb.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mech.cpp", "api.cpp", "kinetics.cu", "noalloc.cu", "forms.cu", "batch.cu", "fd.cu", "hostio.cpp"]
+SOURCES = ["mech.cpp", "api.cpp", "kinetics.cu", "noalloc.cu", "forms.cu", "batch.cu", "fd.cu", "lu.cu", "lu_symbolic.cpp", "hostio.cpp"]
 # jacobian_inst.cu is compiled once per (layout, precision): object name,
 # then its defines (see the file's header)
 JAC_INSTANCES = [

@@ -2,6 +2,7 @@
 // kernels in kinetics.cu.  No host synchronisation, no allocation.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <string>
 
 #include "launch.h"
@@ -40,6 +41,7 @@ extern "C" int pj_workspace_size(const pj_mech* m, int op, int64_t n, size_t* by
     case PJ_OP_VJP:
     case PJ_OP_Y: *bytes = form_workspace_bytes(op, m->dm, n); return PJ_OK;
     case PJ_OP_FD: *bytes = fd_workspace_bytes(m->ns, n); return PJ_OK;
+    case PJ_OP_LU: *bytes = lu_workspace_bytes(m->ns + 1, PJ_F64, n); return PJ_OK;
     default: return fail(PJ_ERR_ARG, "pj_workspace_size: unknown op");
   }
 }
@@ -131,4 +133,36 @@ extern "C" int pj_diag_exp(const pj_mech* m, int64_t n, const double* x, double*
   if (n > 0 && !y_lib) return fail(PJ_ERR_ARG, "pj_diag_exp: null buffer");
   if (n == 0) return PJ_OK;
   return launch_diag_exp(m->dm, n, x, y_ours, y_lib, (cudaStream_t)stream);
+}
+
+extern "C" int pj_lu_info(const pj_mech* m, int32_t* lu_nnz, int32_t* perm) {
+  if (!m || !lu_nnz) return fail(PJ_ERR_ARG, "pj_lu_info: null argument");
+  *lu_nnz = (int32_t)m->lu_rows.size();
+  if (perm) std::memcpy(perm, m->lu_perm.data(), m->lu_perm.size() * sizeof(int32_t));
+  return PJ_OK;
+}
+
+extern "C" int pj_lu_pattern(const pj_mech* m, int32_t* rows, int32_t* cols) {
+  if (!m || !rows || !cols) return fail(PJ_ERR_ARG, "pj_lu_pattern: null argument");
+  std::memcpy(rows, m->lu_rows.data(), m->lu_rows.size() * sizeof(int32_t));
+  std::memcpy(cols, m->lu_cols.data(), m->lu_cols.size() * sizeof(int32_t));
+  return PJ_OK;
+}
+
+extern "C" int pj_lu_factor(const pj_mech* m, int prec, int64_t n, const void* vals, int64_t ld, const double* h,
+                            double gamma, void* lu, int* status, void* work, size_t work_bytes, void* stream) {
+  if (prec != PJ_F64 && prec != PJ_F32) return fail(PJ_ERR_ARG, "pj_lu_factor: prec must be PJ_F64 or PJ_F32");
+  int rc = check_common("pj_lu_factor", m, PJ_CONP, n, ld, vals, vals, lu);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_lu_factor(m->lu, prec, n, vals, ld, h, gamma, lu, status, work, work_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int pj_lu_solve(const pj_mech* m, int prec, int64_t n, const void* lu, int64_t ld, const void* b,
+                           void* x, void* stream) {
+  if (prec != PJ_F64 && prec != PJ_F32) return fail(PJ_ERR_ARG, "pj_lu_solve: prec must be PJ_F64 or PJ_F32");
+  int rc = check_common("pj_lu_solve", m, PJ_CONP, n, ld, lu, b, x);
+  if (rc) return rc;
+  if (n == 0) return PJ_OK;
+  return launch_lu_solve(m->lu, prec, n, lu, ld, b, x, (cudaStream_t)stream);
 }

@@ -68,6 +68,11 @@ int launch_fd_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const dou
                        int64_t ld, double* J, double* dphi, int* status, void* work, size_t work_bytes,
                        cudaStream_t st);
 size_t fd_workspace_bytes(int ns, int64_t n);
+int launch_lu_factor(const DevLu& L, int prec, int64_t n, const void* vals, int64_t ld, const double* hstep,
+                     double gamma, void* lu, int* status, void* work, size_t work_bytes, cudaStream_t st);
+int launch_lu_solve(const DevLu& L, int prec, int64_t n, const void* lu, int64_t ld, const void* b, void* x,
+                    cudaStream_t st);
+size_t lu_workspace_bytes(int N, int prec, int64_t n);
 int launch_diag_exp(const DevMech& m, int64_t n, const double* x, double* y_ours, double* y_lib, cudaStream_t st);
 int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, const double* phi, int64_t ld,
                   double* y, int* status, void* work, size_t work_bytes, cudaStream_t st);

@@ -342,7 +342,7 @@ int mech_build(pj_mech* m) {
   if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
     cudaGetLastError();
     m->device = -1;
-    return PJ_OK;
+    return lu_build(m);
   }
   int dev = 0;
   if ((rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
@@ -372,7 +372,7 @@ int mech_build(pj_mech* m) {
   dm.pos_csc = reinterpret_cast<const int32_t*>(b + o_pcsc);
   dm.perm = reinterpret_cast<const int32_t*>(b + o_perm);
   dm.exp_tab = reinterpret_cast<const double*>(b + o_etab);
-  return PJ_OK;
+  return lu_build(m);
 }
 
 void mech_release(pj_mech* m) {
@@ -381,8 +381,10 @@ void mech_release(pj_mech* m) {
     cudaGetDevice(&cur);
     if (cur != m->device) cudaSetDevice(m->device);
     cudaFree(m->dev_blob);
+    if (m->lu_blob) cudaFree(m->lu_blob);
     if (cur != m->device && cur >= 0) cudaSetDevice(cur);
     m->dev_blob = nullptr;
+    m->lu_blob = nullptr;
   }
 }
 

@@ -78,6 +78,22 @@ struct DevMech {
   const double* exp_tab;          // [256] 2^(j/256), correctly rounded (pj_exp)
 };
 
+// Index tables of the Newton-matrix LU (lu_symbolic.cpp, lu.cu); pivot
+// order k, dense pivot-order positions r*N + c.
+struct DevLu {
+  int32_t N, nnz, lu_nnz, nl;  // nnz: CSR entries of M; nl: strictly lower factor entries
+  const int32_t* perm;         // [N] state-vector index of pivot k
+  const int32_t* rptr;         // [N+1] rows i > k of column k ...
+  const int32_t* ridx;         //   ... ascending
+  const int32_t* cptr;         // [N+1] columns j > k of row k ...
+  const int32_t* cidx;         //   ... ascending
+  const int32_t* m2d;          // [nnz] CSR entry -> dense position
+  const int32_t* l2d;          // [lu_nnz] factor entry (storage order) -> dense position
+  const int32_t* xcol;         // [lu_nnz] state-vector index of the entry's column
+  const int32_t* lptr;         // [N+1] lower row k in storage
+  const int32_t* uptr;         // [N+1] upper row N-1-q in storage (diagonal first)
+};
+
 }  // namespace pj
 
 struct pj_mech {
@@ -94,6 +110,10 @@ struct pj_mech {
   pj::DevMech dm{};
   void* dev_blob = nullptr;
   size_t dev_bytes = 0;
+  // LU of the Newton matrix: pivot order, factor storage (pivot indices)
+  std::vector<int32_t> lu_perm, lu_rows, lu_cols;
+  pj::DevLu lu{};
+  void* lu_blob = nullptr;
 };
 
 namespace pj {
@@ -101,5 +121,6 @@ namespace pj {
 int fail(int code, const std::string& msg);
 int check_cuda(int err, const char* what);
 int mech_build(pj_mech* m);          // pack + pattern + upload
+int lu_build(pj_mech* m);            // LU ordering, fill and tables (after the pattern)
 void mech_release(pj_mech* m);
 }  // namespace pj

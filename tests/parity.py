@@ -43,3 +43,47 @@ def paper_error_norms(J_gpu, J_ref, C_thresh=1e20):
     rel = np.where(mask, np.abs(d) / np.where(mask, np.abs(r), 1.0), 0.0)
     EC_k = np.linalg.norm(rel, axis=0)
     return float(np.linalg.norm(EL_k)), float(np.linalg.norm(EC_k))
+
+
+def lu_dense_from_storage(vals, rows, cols, N):
+    """(L unit lower, U upper) [N, N, n] from factor values in storage order
+    (1 / U_kk in the diagonal slots)."""
+    n = vals.shape[1]
+    L = np.zeros((N, N, n))
+    U = np.zeros((N, N, n))
+    low = rows > cols
+    L[rows[low], cols[low]] = vals[low]
+    L[np.arange(N), np.arange(N)] = 1.0
+    up = rows < cols
+    U[rows[up], cols[up]] = vals[up]
+    d = rows == cols
+    U[rows[d], cols[d]] = 1.0 / vals[d]
+    return L, U
+
+
+def lu_backward_ratio(L, U, A, u, tiny=2.0 ** -1074):
+    """max over entries of |L U - A| / (N u (|L||U|) + tiny (row sums of |L|
+    + column sums of |U| + 1)): at most a small constant for a backward-stable
+    factorisation (computed in float64).  The tiny term (the subnormal
+    spacing of the factors' precision) covers gradual underflow of factor
+    entries, which the relative bound alone does not."""
+    N = A.shape[0]
+    mm = lambda a, b: np.moveaxis(np.matmul(np.moveaxis(a, 2, 0), np.moveaxis(b, 2, 0)), 0, 2)
+    LU = mm(L, U)
+    env = mm(np.abs(L), np.abs(U))
+    under = tiny * (np.abs(L).sum(axis=1)[:, None, :] + np.abs(U).sum(axis=0)[None, :, :] + 1.0)
+    r = np.abs(LU - A)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(r == 0, 0.0, r / (N * u * env + under))
+    return float(q.max())
+
+
+def equilibrated_backward_ratio(M, x, b, D, u):
+    """Normwise backward error of M x = b in the variables scaled by D (the
+    states' own magnitudes, rows and columns), over N u, per state."""
+    N = M.shape[0]
+    At = M * D[None, :, :] / D[:, None, :]
+    xt, bt = x / D, b / D
+    r = np.abs(np.einsum("ijn,jn->in", At, xt) - bt).max(axis=0)
+    den = np.abs(At).sum(axis=1).max(axis=0) * np.abs(xt).max(axis=0) + np.abs(bt).max(axis=0)
+    return r / den / (N * u)

@@ -161,3 +161,29 @@ def test_jacobian_form_rejects_unknown_form(lib, mechs):
     out = C.c_void_p()
     assert lib.pj_mech_with_jacobian_form(h.handle, 7, C.byref(out)) == N.PJ_ERR_ARG
     assert lib.pj_mech_with_jacobian_form(None, 0, C.byref(out)) == N.PJ_ERR_ARG
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "h2co13", "gri53", "usc111"])
+def test_lu_ordering_and_pattern_bit_exact_against_oracle(lib, mechs, name, form):
+    """The Newton-matrix LU's symbolic phase (pivot order, fill, storage
+    order) is index work: identical to the oracle's."""
+    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency") else mechs(name)
+    h = pj.pj_mech_create(m)
+    if form:
+        h = h.with_jacobian_form(pj.PJ_JAC_APPROX)
+    perm, F, (r, c) = oracle.linalg.lu_symbolic(m, oracle.APPROX if form else oracle.EXACT)
+    k, p = h.lu_info()
+    hr, hc = h.lu_pattern()
+    assert k == len(r) == F.sum()
+    assert p.tobytes() == perm.astype(np.int32).tobytes()
+    assert hr.tobytes() == r.tobytes() and hc.tobytes() == c.tobytes()
+
+
+def test_lu_ordering_and_pattern_874_species(lib, mechs):
+    m = mechs("ic5874")
+    h = pj.pj_mech_create(m)
+    perm, F, (r, c) = oracle.linalg.lu_symbolic(m)
+    k, p = h.lu_info()
+    hr, hc = h.lu_pattern()
+    assert k == len(r) and np.array_equal(p, perm) and np.array_equal(hr, r) and np.array_equal(hc, c)

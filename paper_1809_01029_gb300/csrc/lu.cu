@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
   const int NN = N * N;
   T* A = gws ? gws + (int64_t)blockIdx.x * NN : reinterpret_cast<T*>(lu_smem);
   __shared__ int bad;
+  __shared__ T s_inv;
   for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
     if (tid == 0) bad = 0;
     for (int p = tid; p < NN; p += nt) A[p] = T(0);
@@ -59,9 +60,17 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
     if (FROM_J)
       for (int k = tid; k < N; k += nt) A[k * N + k] += T(1);
     __syncthreads();
+    // one thread forms each pivot's reciprocal ahead of its step (the FP64
+    // pipe charges whole warps, so a division in every thread would cost as
+    // much as a large part of the elimination)
+    if (tid == 0) {
+      const T piv = A[0];
+      if (bad_pivot(piv)) bad = 1;
+      s_inv = T(1) / piv;
+    }
+    __syncthreads();
     for (int k = 0; k < N; k++) {
-      const T piv = A[k * N + k];
-      const T inv = T(1) / piv;
+      const T inv = s_inv;
       const int r0 = __ldg(L.rptr + k), nr = __ldg(L.rptr + k + 1) - r0;
       const int c0 = __ldg(L.cptr + k), nc = __ldg(L.cptr + k + 1) - c0;
       for (int a = tid; a < nr; a += nt) {
@@ -69,33 +78,78 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
         A[i * N + k] *= inv;
       }
       __syncthreads();
-      if (nr > 0 && nc > 0) {
-        if (nc >= nt) {
-          for (int cj = tid; cj < nc; cj += nt) {
-            const int j = __ldg(L.cidx + c0 + cj);
-            const T u = A[k * N + j];
-            for (int a = 0; a < nr; a++) {
-              const int i = __ldg(L.ridx + r0 + a);
-              A[i * N + j] = fma_t(-A[i * N + k], u, A[i * N + j]);
-            }
+      // the nr x nc update.  FP64: flattened over every thread so that warps
+      // stay full (the FP64 pipe is the bound and charges idle lanes); pair
+      // p = a * nc + c, walked with stride nt four pairs at a time (distinct
+      // pairs touch distinct entries, so loads go out first).  FP32 (issue
+      // bound): threads over columns, U_kj in a register, rows four at a time.
+      const int tot = nr * nc;
+      if (sizeof(T) == 4 && tot > 0) {
+        const int per = nc >= nt ? 1 : nt / nc;
+        const int a0 = nc >= nt ? 0 : tid / nc;
+        for (int cj = nc >= nt ? tid : tid % nc; cj < nc && a0 < per; cj += nc >= nt ? nt : nc) {
+          const int j = __ldg(L.cidx + c0 + cj);
+          const T u = A[k * N + j];
+          int a = a0;
+          for (; a + 3 * per < nr; a += 4 * per) {
+            const int i0 = __ldg(L.ridx + r0 + a), i1 = __ldg(L.ridx + r0 + a + per);
+            const int i2 = __ldg(L.ridx + r0 + a + 2 * per), i3 = __ldg(L.ridx + r0 + a + 3 * per);
+            const T l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
+            const T v0 = A[i0 * N + j], v1 = A[i1 * N + j], v2 = A[i2 * N + j], v3 = A[i3 * N + j];
+            A[i0 * N + j] = fma_t(-l0, u, v0);
+            A[i1 * N + j] = fma_t(-l1, u, v1);
+            A[i2 * N + j] = fma_t(-l2, u, v2);
+            A[i3 * N + j] = fma_t(-l3, u, v3);
           }
-        } else {
-          const int per = nt / nc;
-          const int cj = tid % nc, a0 = tid / nc;
-          if (a0 < per) {
-            const int j = __ldg(L.cidx + c0 + cj);
-            const T u = A[k * N + j];
-            for (int a = a0; a < nr; a += per) {
-              const int i = __ldg(L.ridx + r0 + a);
-              A[i * N + j] = fma_t(-A[i * N + k], u, A[i * N + j]);
-            }
+          for (; a < nr; a += per) {
+            const int i = __ldg(L.ridx + r0 + a);
+            A[i * N + j] = fma_t(-A[i * N + k], u, A[i * N + j]);
           }
+          if (nc < nt) break;  // one column per thread in that case
+        }
+      } else if (tid < tot) {
+        const int di = nt / nc, dj = nt - di * nc;
+        int ia = tid / nc, jc = tid - ia * nc;
+        auto step = [&]() {
+          ia += di;
+          jc += dj;
+          if (jc >= nc) {
+            jc -= nc;
+            ia++;
+          }
+        };
+        int p = tid;
+        for (; p + 3 * nt < tot; p += 4 * nt) {
+          const int i0 = __ldg(L.ridx + r0 + ia), j0 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i1 = __ldg(L.ridx + r0 + ia), j1 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i2 = __ldg(L.ridx + r0 + ia), j2 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i3 = __ldg(L.ridx + r0 + ia), j3 = __ldg(L.cidx + c0 + jc);
+          step();
+          const T l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
+          const T u0 = A[k * N + j0], u1 = A[k * N + j1], u2 = A[k * N + j2], u3 = A[k * N + j3];
+          const T v0 = A[i0 * N + j0], v1 = A[i1 * N + j1], v2 = A[i2 * N + j2], v3 = A[i3 * N + j3];
+          A[i0 * N + j0] = fma_t(-l0, u0, v0);
+          A[i1 * N + j1] = fma_t(-l1, u1, v1);
+          A[i2 * N + j2] = fma_t(-l2, u2, v2);
+          A[i3 * N + j3] = fma_t(-l3, u3, v3);
+        }
+        for (; p < tot; p += nt) {
+          const int i = __ldg(L.ridx + r0 + ia), j = __ldg(L.cidx + c0 + jc);
+          A[i * N + j] = fma_t(-A[i * N + k], A[k * N + j], A[i * N + j]);
+          step();
         }
       }
       __syncthreads();
       if (tid == 0) {
-        if (bad_pivot(piv)) bad = 1;
         A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
+        if (k + 1 < N) {
+          const T piv = A[(k + 1) * N + k + 1];
+          if (bad_pivot(piv)) bad = 1;
+          s_inv = T(1) / piv;
+        }
       }
       __syncthreads();
     }
@@ -120,22 +174,33 @@ __global__ void __launch_bounds__(128) k_lu_solve(DevLu L, int64_t n, const T* _
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     T* X = SMEM_X ? reinterpret_cast<T*>(lu_smem) + threadIdx.x : x + s;
     const int64_t xs = SMEM_X ? blockDim.x : ld;
+    // sum over storage entries [e, e1) of value * X[column], four independent
+    // partial sums so that the factor loads stream
+    auto dot = [&](int e, int e1) -> T {
+      T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+      for (; e + 3 < e1; e += 4) {
+        const int c0 = __ldg(L.xcol + e), c1 = __ldg(L.xcol + e + 1);
+        const int c2 = __ldg(L.xcol + e + 2), c3 = __ldg(L.xcol + e + 3);
+        p0 = fma_t(lu[(int64_t)e * ld + s], X[(int64_t)c0 * xs], p0);
+        p1 = fma_t(lu[(int64_t)(e + 1) * ld + s], X[(int64_t)c1 * xs], p1);
+        p2 = fma_t(lu[(int64_t)(e + 2) * ld + s], X[(int64_t)c2 * xs], p2);
+        p3 = fma_t(lu[(int64_t)(e + 3) * ld + s], X[(int64_t)c3 * xs], p3);
+      }
+      for (; e < e1; e++) p0 = fma_t(lu[(int64_t)e * ld + s], X[(int64_t)__ldg(L.xcol + e) * xs], p0);
+      return (p0 + p1) + (p2 + p3);
+    };
     // forward: y_k = b_perm[k] - sum_{j<k} L_kj y_j, y kept at X[perm[k]]
     for (int k = 0; k < N; k++) {
       const int pk = __ldg(L.perm + k);
-      T acc = b[(int64_t)pk * ld + s];
-      for (int e = __ldg(L.lptr + k), e1 = __ldg(L.lptr + k + 1); e < e1; e++)
-        acc = fma_t(-lu[(int64_t)e * ld + s], X[(int64_t)__ldg(L.xcol + e) * xs], acc);
-      X[(int64_t)pk * xs] = acc;
+      const T bk = b[(int64_t)pk * ld + s];
+      X[(int64_t)pk * xs] = bk - dot(__ldg(L.lptr + k), __ldg(L.lptr + k + 1));
     }
     // backward: z_k = (y_k - sum_{j>k} U_kj z_j) / U_kk
     for (int q = 0; q < N; q++) {
       const int e0 = __ldg(L.uptr + q), e1 = __ldg(L.uptr + q + 1);
       const int pk = __ldg(L.perm + (N - 1 - q));
-      T acc = X[(int64_t)pk * xs];
-      for (int e = e0 + 1; e < e1; e++)
-        acc = fma_t(-lu[(int64_t)e * ld + s], X[(int64_t)__ldg(L.xcol + e) * xs], acc);
-      X[(int64_t)pk * xs] = acc * lu[(int64_t)e0 * ld + s];
+      const T yk = X[(int64_t)pk * xs];
+      X[(int64_t)pk * xs] = (yk - dot(e0 + 1, e1)) * lu[(int64_t)e0 * ld + s];
     }
     if (SMEM_X)
       for (int v = 0; v < N; v++) x[(int64_t)v * ld + s] = X[(int64_t)v * xs];
@@ -161,7 +226,7 @@ static LuPlan lu_plan(int N, size_t esize, int64_t n) {
     p.smem = true;
     p.dyn = dense;
     const int ctas = std::max(1, std::min(16, (int)(kSmemPerSm / (dense + 1024 + 256))));
-    int warps = (8 + ctas - 1) / ctas;  // at least 8 warps per SM
+    int warps = (16 + ctas - 1) / ctas;  // at least 16 warps per SM
     warps = std::max(1, std::min(8, warps));
     p.threads = 32 * warps;
     p.grid = (int)std::min<int64_t>(states, (int64_t)sm_count() * ctas);

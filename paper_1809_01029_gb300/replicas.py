@@ -4,7 +4,9 @@ States are independent (one state per thread, Sec. 2.1), so a batch shards
 into contiguous chunks with no exchange on the data path; a shard is simply
 (pointer offset, count) on the same C ABI.  These helpers split a batch over
 ranks, take the maximum of per-rank times and, for callers that want every
-rank to hold all outputs, all-gather state-major outputs.
+rank to hold all outputs, all-gather state-major outputs; the adjoint's
+parameter gradient, a sum over states, is the one quantity that needs an
+exchange (an all-reduce of Nr x 3 values).
 """
 from __future__ import annotations
 
@@ -43,3 +45,12 @@ def gather_states(local, n_total: int, dist):
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf.contiguous())
     return torch.cat([p[:, :c] for p, c in zip(parts, counts)], dim=1)
+
+
+def allreduce_sum(t, dist=None):
+    """Sum a tensor over the process group in place (e.g. the VJP's per-shard
+    parameter gradient g_theta [Nr, 3]); returns it."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t

@@ -33,7 +33,11 @@ def _worker(rank, world, port, q):
         f_local = oracle.source_terms(m, synth.CONP, phi[:, lo:hi], par[lo:hi])
         f_all = replicas.gather_states(torch.from_numpy(f_local), n, dist).numpy()
         t_max = replicas.max_over_ranks(10.0 + rank, dist)
-        q.put((rank, lo, hi, f_all, t_max))
+        # adjoint parameter gradient: per-shard sums, all-reduced
+        uw, uT = synth.make_cotangents(m.n_species, n, 6)
+        _, g_th = oracle.vjp(m, synth.CONP, phi[:, lo:hi], par[lo:hi], uw[:, lo:hi], uT[lo:hi])
+        g_all = replicas.allreduce_sum(torch.from_numpy(np.ascontiguousarray(g_th)), dist).numpy()
+        q.put((rank, lo, hi, f_all, t_max, g_all))
     finally:
         dist.destroy_process_group()
 
@@ -53,7 +57,7 @@ def test_two_gloo_ranks_shard_gather_and_time():
         p.join(timeout=60)
         assert p.exitcode == 0
     res.sort(key=lambda x: x[0])
-    (_, lo0, hi0, f0, t0), (_, lo1, hi1, f1, t1) = res
+    (_, lo0, hi0, f0, t0, g0), (_, lo1, hi1, f1, t1, g1) = res
     assert (lo0, hi0, lo1, hi1) == (0, 19, 19, 37)
     assert t0 == t1 == 11.0
     m = synth.make_mechanism("h2co13")
@@ -61,6 +65,10 @@ def test_two_gloo_ranks_shard_gather_and_time():
     ref = oracle.source_terms(m, synth.CONP, phi, par)
     assert np.array_equal(f0, f1)
     assert np.allclose(f0, ref, rtol=1e-13, atol=0)
+    uw, uT = synth.make_cotangents(m.n_species, 37, 6)
+    _, g_ref = oracle.vjp(m, synth.CONP, phi, par, uw, uT)
+    assert np.array_equal(g0, g1)
+    assert np.allclose(g0, g_ref, rtol=1e-12, atol=1e-12 * np.abs(g_ref).max())
 
 
 @pytest.mark.parametrize("n,world", [(0, 3), (1, 4), (10, 3), (1048576, 8)])

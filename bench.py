@@ -157,6 +157,50 @@ def _time(torch, stream, fn, reps=5):
     return a.elapsed_time(b) / reps
 
 
+def lu_work_per_state(h):
+    """FP64 work of one LU factorisation in DFMA-equivalents: for pivot k,
+    |rows| x |cols| fused multiply-adds and |rows| multiplies, and one
+    divide (rows/cols: the fill pattern's column below and row right of k)."""
+    r, c = h.lu_pattern()
+    N = h.n_species + 1
+    rows = np.bincount(c[r > c], minlength=N)
+    cols = np.bincount(r[c > r], minlength=N)
+    return float(np.sum(rows * cols) + np.sum(rows) + N * W_DIV)
+
+
+# ncu DRAM bytes per state of a kernel, recorded in profiles/ together with a
+# hash of the kernel sources at capture time; a number is only used while
+# the sources are unchanged.
+PROFILE_OF = {("jac_csr", "gri53"): "k_jacobian_tm_gri53.md", ("source", "gri53"): "k_source_terms_gri53.md",
+              ("lu", "gri53"): "k_lu_factor_gri53.md"}
+
+
+def sources_hash():
+    import hashlib
+    d = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1809_01029_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            d.update(f.encode())
+            d.update(open(os.path.join(csrc, f), "rb").read())
+    d.update(open(os.path.join(ROOT, "include", "pyjac_gb.h"), "rb").read())
+    return d.hexdigest()[:16]
+
+
+def kernel_traffic(op, mech_name):
+    name = PROFILE_OF.get((op, mech_name))
+    if not name:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    import re
+    m = re.search(r"traffic_bytes_per_state:\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]+)", open(path).read())
+    if not m or m.group(2) != sources_hash():
+        return None
+    return float(m.group(1))
+
+
 def lu_workloads(pj, synth, torch, dev, stream):
     """States/s of the Newton-matrix LU factorisation and solve: FP64 with
     M = I - h J formed from the FP64 Jacobian (53 species), and FP32 of the
@@ -366,7 +410,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi clock samples (default: a temp dir)")
     ap.add_argument("--op", default="jac_csr",
-                    choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp"],
+                    choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp", "lu"],
                     help="what one step evaluates (default: source terms + CSR Jacobian)")
     ap.add_argument("--mode", default="conp", choices=["conp", "conv"])
     args = ap.parse_args()
@@ -388,7 +432,7 @@ def main():
         dist.init_process_group("nccl")
     pj.load_library()
     mech_name = {"newton": "usc111"}.get(args.op, "gri53")
-    default_n = {"newton": 262144, "vjp": 65536}.get(args.op, 1048576)
+    default_n = {"newton": 262144, "vjp": 65536, "lu": 262144}.get(args.op, 1048576)
     m = synth.make_mechanism(mech_name)
     h = pj.pj_mech_create(m)
     n = args.n or default_n
@@ -418,6 +462,14 @@ def main():
     if args.op == "vjp":
         wb = h.workspace_size(pj.PJ_OP_VJP, n)
         work = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    if args.op == "lu":
+        # factor M = I - h J formed from the FP64 CSR Jacobian of the states
+        hstep = torch.from_numpy(synth.make_step_sizes(n, 2018 + 3)).to(dev)
+        pj.pj_eval_jacobian_sparse(h, mode, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)
+        lu_nnz, _ = h.lu_info()
+        lu = torch.empty((lu_nnz, n), dtype=torch.float64, device=dev)
+        wb = h.workspace_size(pj.PJ_OP_LU, n)
+        work = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
 
     def step():
         if args.op == "source":
@@ -429,6 +481,8 @@ def main():
             pj.pj_vjp(h, mode, n, par, phi, n, u_w, u_T, dphi, vals, g_th, status, work, wb, stream)
         elif args.op == "jac_dense":
             pj.pj_eval_jacobian_dense(h, mode, n, par, phi, n, vals, dphi, status, work, wb, stream)
+        elif args.op == "lu":
+            pj.pj_lu_factor(h, pj.PJ_F64, n, vals, n, lu, hstep, 1.0, status, work, wb, stream)
         else:
             fmt = pj.PJ_CSC if args.op == "jac_csc" else pj.PJ_CSR
             pj.pj_eval_jacobian_sparse(h, mode, fmt, n, par, phi, n, vals, dphi, status, work, wb, stream)
@@ -460,16 +514,23 @@ def main():
     assert int(status.item()) == 0, "invalid states in the benchmark batch"
 
     # roofline of the (single) kernel of the step: FP64 pipe
-    fp64_work = fp64_work_per_state(m, jacobian=args.op not in ("source",))
+    if args.op == "lu":
+        fp64_work = lu_work_per_state(h)
+    else:
+        fp64_work = fp64_work_per_state(m, jacobian=args.op not in ("source",))
     achieved = fp64_work * n / (ms * 1e-3) / 1e9     # G DFMA-equivalent / s
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": {"source": "k_source_terms", "vjp": "k_vjp"}.get(args.op, "k_jacobian"),
+                "kernel": {"source": "k_source_terms", "vjp": "k_vjp", "lu": "k_lu_factor"}.get(args.op, "k_jacobian"),
                 "work_per_state": fp64_work,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
+    tr = kernel_traffic(args.op, mech_name)
+    if tr is not None:
+        roofline["traffic"] = tr * n
+        roofline["traffic_source"] = "ncu dram bytes per state of the current kernel sources x states"
 
     variants = {}
     if not args.no_variants and args.op == "jac_csr":
@@ -561,7 +622,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": {"newton": "usc111_256k", "vjp": "gri53_vjp64k"}.get(args.op, WORKLOAD),
+            "config": {"workload": {"newton": "usc111_256k", "vjp": "gri53_vjp64k", "lu": "gri53_lu256k"}.get(args.op, WORKLOAD),
                    "mechanism": "synthetic %d species / %d reactions (seed %d)" % (
                        m.n_species, m.n_reactions, synth.SPECS[mech_name].seed),
                        "states_per_gpu": n, "mode": args.mode.upper(), "op": args.op,
@@ -570,6 +631,7 @@ def main():
                                   "jac_csr": "source terms + CSR Jacobian (nnz %d)" % h.nnz,
                                   "jac_csc": "source terms + CSC Jacobian (nnz %d)" % h.nnz,
                                   "jac_dense": "source terms + dense Jacobian (%d entries)" % (N1 * N1),
+                                  "lu": "FP64 LU factors of I - h J (%d values)" % h.lu_info()[0],
                                   "source": "source terms"}[args.op],
                        "l2": "inputs and outputs larger than L2 (%.1f GB per step)" % ((h.nnz + 2 * (m.n_species + 1)) * n * 8 / 1e9),
                        "parallelism": f"replicas x{world}"},

@@ -37,7 +37,8 @@ R_CAL = 1.98720425864083      # cal / (mol K); activation energies are in cal/mo
 P_ATM = 101325.0              # Pa, standard-state pressure of the equilibrium constant
 
 CONP, CONV = 0, 1
-ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI = 0, 1, 2, 3, 4
+ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI, PLOG, CHEB = 0, 1, 2, 3, 4, 5, 6
+FALLOFF = (LINDEMANN, TROE, SRI)
 
 
 def _re(x):
@@ -144,6 +145,45 @@ def sri_F(mech, i, T, Pr):
     return d * (a * np.exp(-b / T) + np.exp(-T / c)) ** X * T ** e
 
 
+def plog_lnk(mech, i, T, P):
+    """ln k of a P-log reaction: the Arrhenius rates tabulated at pressures
+    P_1 < .. < P_n, interpolated linearly in ln P between neighbours and held
+    at the end values below P_1 and from P_n on.  Segment m covers
+    [P_m, P_m+1), chosen by the real part of ln P."""
+    tab = mech.plog_table(i)
+    lnT = np.log(T)
+    lnks = [np.log(A) + b * lnT - Ea / (R_CAL * T) for _, A, b, Ea in tab]
+    lnPs = np.log(tab[:, 0])
+    x = np.log(P)
+    xr = _re(x) * np.ones(np.shape(T))
+    out = lnks[0] * np.ones(np.shape(T), dtype=np.result_type(lnks[0], x))
+    for m in range(len(tab) - 1):
+        inside = (xr >= lnPs[m]) & (xr < lnPs[m + 1])
+        w = (x - lnPs[m]) / (lnPs[m + 1] - lnPs[m])
+        out = np.where(inside, lnks[m] + (lnks[m + 1] - lnks[m]) * w, out)
+    return np.where(xr >= lnPs[-1], lnks[-1], out)
+
+
+def cheb_log10k(mech, i, T, P):
+    """log10 k of a Chebyshev reaction: sum_t sum_p a_tp phi_t(T~) phi_p(P~),
+    phi_n the Chebyshev polynomials of the first kind (phi_0 = 1, phi_1 = x,
+    phi_n = 2 x phi_{n-1} - phi_{n-2}), T~ = (2/T - 1/T_min - 1/T_max) /
+    (1/T_max - 1/T_min), P~ = (2 log10 P - log10 P_min - log10 P_max) /
+    (log10 P_max - log10 P_min)."""
+    Tmin, Tmax, Pmin, Pmax = mech.cheb_range[i]
+    a = mech.cheb_table(i)
+    Tt = (2.0 / T - 1.0 / Tmin - 1.0 / Tmax) / (1.0 / Tmax - 1.0 / Tmin)
+    Pt = (2.0 * np.log10(P) - np.log10(Pmin) - np.log10(Pmax)) / (np.log10(Pmax) - np.log10(Pmin))
+
+    def basis(x, n):
+        ph = [np.ones_like(x), x]
+        while len(ph) < n:
+            ph.append(2.0 * x * ph[-1] - ph[-2])
+        return ph[:n]
+    pt, pp = basis(Tt, a.shape[0]), basis(Pt * np.ones_like(Tt), a.shape[1])
+    return sum(a[t, q] * pt[t] * pp[q] for t in range(a.shape[0]) for q in range(a.shape[1]))
+
+
 def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_bath=False):
     """All intermediate quantities of the source-term evaluation.
 
@@ -187,16 +227,26 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_ba
     Rf = np.empty(shape, dtype=dt)
     Rr = np.empty(shape, dtype=dt)
     for i in range(nr):
-        kf[i] = arrhenius(A[i], beta[i], Ea[i], T)
-        if mech.reversible[i]:
+        kind = mech.kind[i]
+        chem = kind in FALLOFF and bool(mech.chem[i])
+        if kind == PLOG:
+            kf[i] = np.exp(plog_lnk(mech, i, T, P))
+        elif kind == CHEB:
+            kf[i] = 10.0 ** cheb_log10k(mech, i, T, P)
+        elif chem:                               # chemically activated: base rate k0
+            kf[i] = arrhenius(mech.A0[i], mech.beta0[i], mech.Ea0[i], T)
+        else:
+            kf[i] = arrhenius(A[i], beta[i], Ea[i], T)
+        if mech.reversible[i] and mech.rev_explicit[i]:
+            kr[i] = arrhenius(*mech.rev_arr[i], T)
+        elif mech.reversible[i]:
             dg = sum(nu[k, i] * g[k] for k in range(ns) if nu[k, i] != 0)
             dn = float(nu[:, i].sum())
             Kc = np.exp(-dg) * (P_ATM / (R * T)) ** dn
             kr[i] = kf[i] / Kc
         else:
             kr[i] = 0.0
-        kind = mech.kind[i]
-        if kind == ELEMENTARY:
+        if kind in (ELEMENTARY, PLOG, CHEB):
             cmod[i] = 1.0
         else:
             M = third_body_alpha(mech, i) @ Cr.reshape(ns, -1)
@@ -207,17 +257,22 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_ba
                 cmod[i] = M
             else:
                 k0 = arrhenius(mech.A0[i], mech.beta0[i], mech.Ea0[i], T)
-                Pr = k0 * M / kf[i]
+                kinf = arrhenius(A[i], beta[i], Ea[i], T)
+                Pr = k0 * M / kinf
                 if kind == LINDEMANN:
                     F = 1.0
                 elif kind == TROE:
                     F = troe_F(mech, i, T, Pr)
                 else:
                     F = sri_F(mech, i, T, Pr)
-                # Pr/(1+Pr) written as 1/(1+1/Pr): the same function, but its
-                # complex-step derivative avoids the cancellation
-                # (1+Pr) dPr - Pr dPr that loses digits for large Pr
-                cmod[i] = F / (1 + 1 / Pr)
+                if chem:
+                    # chemically activated: k = k0 F / (1 + Pr)
+                    cmod[i] = F / (1 + Pr)
+                else:
+                    # Pr/(1+Pr) written as 1/(1+1/Pr): the same function, but
+                    # its complex-step derivative avoids the cancellation
+                    # (1+Pr) dPr - Pr dPr that loses digits for large Pr
+                    cmod[i] = F / (1 + 1 / Pr)
         fwd = kf[i]
         for k, v in mech.reactants(i):
             fwd = fwd * Cr[k] ** v
@@ -467,7 +522,7 @@ def dependence_set(mech, i, form=EXACT):
         members += [k for k, _ in mech.products(i)]
     dep.update(k for k in members if k != bath)
     dense = bath in members
-    if mech.kind[i] != ELEMENTARY:
+    if mech.kind[i] in (THIRD_BODY,) + FALLOFF:
         a = third_body_alpha(mech, i)
         ref = 1.0 if form == APPROX else a[bath]
         dep.update(k for k in range(ns - 1) if a[k] != ref)

@@ -3,7 +3,7 @@
 Shared by the CPU oracle and the CUDA path; holds none of the evaluated
 method's arithmetic.
 """
-from .mechanism import (ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI, KIND_NAMES, MAX_SP,
+from .mechanism import (ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI, PLOG, CHEB, KIND_NAMES, MAX_SP,
                         ELEMENTS, ATOMIC_MASS, Mechanism, MechSpec, SPECS, make_mechanism,
                         build_mechanism)
 from .states import (CONP, CONV, P_ATM, WORKLOADS, Workload, make_states, ragged_batch_sizes,

@@ -34,9 +34,9 @@ ATOMIC_MASS = np.array([1.008, 15.999, 12.011, 14.007, 39.948])
 R_GAS = 8314.46261815324  # J / (kmol K)
 
 # reaction kinds
-ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI = 0, 1, 2, 3, 4
-KIND_NAMES = {ELEMENTARY: "ELEMENTARY", THIRD_BODY: "THIRD_BODY",
-              LINDEMANN: "LINDEMANN", TROE: "TROE", SRI: "SRI"}
+ELEMENTARY, THIRD_BODY, LINDEMANN, TROE, SRI, PLOG, CHEB = 0, 1, 2, 3, 4, 5, 6
+KIND_NAMES = {ELEMENTARY: "ELEMENTARY", THIRD_BODY: "THIRD_BODY", LINDEMANN: "LINDEMANN", TROE: "TROE",
+              SRI: "SRI", PLOG: "PLOG", CHEB: "CHEBYSHEV"}
 MAX_SP = 4  # distinct species per reaction side supported by the format
 
 
@@ -75,6 +75,44 @@ class Mechanism:
     eff_sp: np.ndarray               # int [n_eff]
     eff_val: np.ndarray              # [n_eff] absolute efficiency alpha
     elements: tuple = ELEMENTS
+    # less common reaction types (absent unless given)
+    chem: np.ndarray = None          # bool [Nr]: chemically-activated falloff (rate k0 F / (1 + Pr))
+    rev_explicit: np.ndarray = None  # bool [Nr]: reverse rate from rev_arr instead of K_c
+    rev_arr: np.ndarray = None       # [Nr, 3]: reverse A, beta, Ea
+    plog_ptr: np.ndarray = None      # int [Nr+1]: P-log entries of each reaction
+    plog: np.ndarray = None          # [n_plog, 4]: P [Pa], A, beta, Ea; P ascending per reaction
+    cheb_ptr: np.ndarray = None      # int [Nr+1]: offsets into cheb_coef
+    cheb_shape: np.ndarray = None    # int [Nr, 2]: N_T, N_P
+    cheb_range: np.ndarray = None    # [Nr, 4]: T_min, T_max [K], P_min, P_max [Pa]
+    cheb_coef: np.ndarray = None     # row-major N_T x N_P per reaction: log10 k, k in SI-kmol units
+
+    def __post_init__(self):
+        nr = len(self.kind)
+        if self.chem is None:
+            self.chem = np.zeros(nr, dtype=bool)
+        if self.rev_explicit is None:
+            self.rev_explicit = np.zeros(nr, dtype=bool)
+        if self.rev_arr is None:
+            self.rev_arr = np.zeros((nr, 3))
+        if self.plog_ptr is None:
+            self.plog_ptr = np.zeros(nr + 1, dtype=np.int64)
+        if self.plog is None:
+            self.plog = np.zeros((0, 4))
+        if self.cheb_ptr is None:
+            self.cheb_ptr = np.zeros(nr + 1, dtype=np.int64)
+        if self.cheb_shape is None:
+            self.cheb_shape = np.zeros((nr, 2), dtype=np.int64)
+        if self.cheb_range is None:
+            self.cheb_range = np.zeros((nr, 4))
+        if self.cheb_coef is None:
+            self.cheb_coef = np.zeros(0)
+
+    def plog_table(self, i: int) -> np.ndarray:
+        return self.plog[self.plog_ptr[i]:self.plog_ptr[i + 1]]
+
+    def cheb_table(self, i: int) -> np.ndarray:
+        nT, nP = self.cheb_shape[i]
+        return self.cheb_coef[self.cheb_ptr[i]:self.cheb_ptr[i + 1]].reshape(nT, nP)
 
     @property
     def n_species(self) -> int:
@@ -339,7 +377,7 @@ def make_mechanism(spec: MechSpec | str) -> Mechanism:
     # in real mechanisms (H2, H2O, CO, ... carry the same efficiencies in
     # every pressure-dependent reaction); each reaction picks up to 3 of them
     colliders = rng.choice(ns - 1, size=min(6, ns - 1), replace=False)
-    # a non-unit bath-gas efficiency makes whole Jacobian rows dense (Sec. 3.3);
+    # a non-unit bath-gas efficiency makes whole Jacobian rows dense (Sec. 3.4);
     # it is kept to about four reactions per mechanism (probability <= 0.1)
     n_pd = int(np.sum(kind != ELEMENTARY))
     p_bath = min(0.1, 4.0 / max(n_pd, 1))
@@ -375,7 +413,10 @@ def build_mechanism(name, species_comp, reactions, nasa=None, seed=7) -> Mechani
     species_comp: list of composition tuples over ELEMENTS (last = bath gas).
     reactions: list of dicts with keys reac, prod (lists of (species, nu)),
       kind, rev, A, beta, Ea and optionally A0, beta0, Ea0, troe (3 or 4
-      values), sri (5 values), eff ({species: alpha}).
+      values), sri (5 values), eff ({species: alpha}), chem (bool),
+      rev_arr ((A, beta, Ea) of an explicit reverse rate), plog (list of
+      (P [Pa], A, beta, Ea)), cheb (dict with T=(T_min, T_max), P=(P_min,
+      P_max) [Pa], coef=[[...]] (N_T x N_P, log10 k)).
     nasa: optional (low [Ns,7], high [Ns,7]); otherwise random smooth fits.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -401,8 +442,22 @@ def build_mechanism(name, species_comp, reactions, nasa=None, seed=7) -> Mechani
                   sri=np.zeros((nr, 5)), eff_ptr=np.zeros(nr + 1, dtype=np.int64),
                   eff_sp=np.zeros(0, dtype=np.int64), eff_val=np.zeros(0))
     eff_sp, eff_val = [], []
+    plog, cheb = [], []
     for i, r in enumerate(reactions):
         m.kind[i] = r.get("kind", ELEMENTARY)
+        m.chem[i] = bool(r.get("chem", False))
+        if "rev_arr" in r:
+            m.rev_explicit[i] = True
+            m.rev_arr[i] = r["rev_arr"]
+        for e in r.get("plog", []):
+            plog.append(list(e))
+        m.plog_ptr[i + 1] = len(plog)
+        if "cheb" in r:
+            c = np.array(r["cheb"]["coef"], dtype=float)
+            m.cheb_shape[i] = c.shape
+            m.cheb_range[i] = list(r["cheb"]["T"]) + list(r["cheb"]["P"])
+            cheb += list(c.ravel())
+        m.cheb_ptr[i + 1] = len(cheb)
         m.reversible[i] = bool(r.get("rev", True))
         for s, (k, n) in enumerate(r["reac"]):
             m.reac_sp[i, s], m.reac_nu[i, s] = k, n
@@ -422,4 +477,6 @@ def build_mechanism(name, species_comp, reactions, nasa=None, seed=7) -> Mechani
         m.eff_ptr[i + 1] = len(eff_sp)
     m.eff_sp = np.array(eff_sp, dtype=np.int64)
     m.eff_val = np.array(eff_val, dtype=float)
+    m.plog = np.array(plog, dtype=float).reshape(-1, 4)
+    m.cheb_coef = np.array(cheb, dtype=float)
     return m

@@ -139,13 +139,48 @@ def pin_approx(K):
     return bool(ok)
 
 
+def pin_types(K):
+    """P-log at a geometric-mean pressure, a Chebyshev rate against numpy's
+    chebval2d, a chemically-activated rate and an explicit reverse rate, each
+    worked outside the oracle."""
+    R, Rc = 8314.46261815324, 1.98720425864083
+    arr = lambda A, b, E, T: A * T ** b * math.exp(-E / (Rc * T))
+    ok = True
+    T, P = 1100.0, math.sqrt(1.0e4 * 1.0e5)
+    ntot = P / (R * T)
+    X = np.full(10, 0.1)
+    phi = np.concatenate([[T, 1.0], X[:-1] * ntot])[:, None]
+    tab = [(1.0e4, 7.0e10, 0.0, 300.0), (1.0e5, 2.0e11, -0.2, 500.0)]
+    m = tm.single(dict(reac=[(tm.H, 1), (tm.HO2, 1)], prod=[(tm.OH, 2)], A=1.0, kind=synth.PLOG, plog=tab))
+    k = math.sqrt(arr(*tab[0][1:], T) * arr(*tab[1][1:], T))
+    ok &= abs(K.rates(m, 0, phi, np.array([P]))["kf"][0, 0] - k) <= 1e-11 * k
+    coef = np.array([[9.0, 0.3], [-0.7, 0.1], [0.05, -0.02]])
+    m = tm.single(dict(reac=[(tm.OH, 1), (tm.H2, 1)], prod=[(tm.H2O, 1), (tm.H, 1)], A=1.0, kind=synth.CHEB,
+                       cheb=dict(T=(300.0, 3000.0), P=(1.0e3, 1.0e7), coef=coef)))
+    Tt = (2 / T - 1 / 300.0 - 1 / 3000.0) / (1 / 3000.0 - 1 / 300.0)
+    Pt = (2 * math.log10(P) - 3.0 - 7.0) / 4.0
+    k = 10.0 ** np.polynomial.chebyshev.chebval2d(Tt, Pt, coef)
+    ok &= abs(K.rates(m, 0, phi, np.array([P]))["kf"][0, 0] - k) <= 1e-11 * k
+    m = tm.single(dict(reac=[(tm.H, 1), (tm.O2, 1)], prod=[(tm.HO2, 1)], A=5.0e9, beta=0.4, kind=synth.LINDEMANN,
+                       chem=True, rev=False, A0=6.0e14, beta0=-1.7, Ea0=500.0))
+    k0, kinf = arr(6.0e14, -1.7, 500.0, T), arr(5.0e9, 0.4, 0.0, T)
+    Pr = k0 * ntot / kinf
+    q = k0 / (1 + Pr) * (0.1 * ntot) ** 2
+    ok &= abs(K.rates(m, 0, phi, np.array([P]))["q"][0, 0] - q) <= 1e-11 * q
+    m = tm.single(dict(reac=[(tm.H, 1), (tm.O2, 1)], prod=[(tm.OH, 1), (tm.O, 1)], A=2.0e11, beta=-0.3,
+                       Ea=15000.0, rev_arr=(1.5e10, 0.1, 800.0)))
+    k = arr(1.5e10, 0.1, 800.0, T)
+    ok &= abs(K.rates(m, 0, phi, np.array([P]))["kr"][0, 0] - k) <= 1e-11 * k
+    return bool(ok)
+
+
 def all_pins(K, mechs):
     g = mechs("h2co13")
     a = tm.all_kinds()
     return dict(equilibrium=pin_equilibrium(K, g), thermo=pin_thermo(K, g),
                 cons_conp=pin_conservation(K, a, 0), cons_conv=pin_conservation(K, a, 1),
                 single=pin_single_rate(K), third_body=pin_third_body(K), troe=pin_troe_center(K),
-                approx=pin_approx(K))
+                approx=pin_approx(K), types=pin_types(K))
 
 
 MUTATIONS = [
@@ -168,6 +203,11 @@ MUTATIONS = [
     ("        Cr[-1] = _re(C[-1])", "        Cr = _re(C)"),
     ("ref = 1.0 if form == APPROX else a[bath]", "ref = a[bath]"),
     ("    if dense and form != APPROX:", "    if dense:"),
+    # less common reaction types
+    ("        w = (x - lnPs[m]) / (lnPs[m + 1] - lnPs[m])", "        w = (np.exp(x) - tab[m, 0]) / (tab[m + 1, 0] - tab[m, 0])"),
+    ("    Tt = (2.0 / T - 1.0 / Tmin - 1.0 / Tmax) / (1.0 / Tmax - 1.0 / Tmin)", "    Tt = (2.0 * T - Tmin - Tmax) / (Tmax - Tmin)"),
+    ("                    cmod[i] = F / (1 + Pr)", "                    cmod[i] = F / (1 + 1 / Pr)"),
+    ("        if mech.reversible[i] and mech.rev_explicit[i]:", "        if False:"),
 ]
 
 

@@ -71,6 +71,8 @@ extern "C" {
 #define PJ_LINDEMANN 2
 #define PJ_TROE 3
 #define PJ_SRI 4
+#define PJ_PLOG 5    /* pressure-dependent Arrhenius (P-log) */
+#define PJ_CHEB 6    /* Chebyshev polynomial in 1/T and log P */
 
 #define PJ_MAX_SP 4 /* distinct species per reaction side */
 
@@ -83,7 +85,7 @@ typedef struct pj_mech pj_mech;
  *   T_mid[Ns]             NASA-7 range switch: low coefficients iff T < T_mid
  *   nasa_low[Ns*7], nasa_high[Ns*7]  a0..a6 (cp/R = a0 + a1 T + .. + a4 T^4,
  *                         h/RT adds a5/T, s/R adds a6)
- *   kind[Nr]              PJ_ELEMENTARY .. PJ_SRI
+ *   kind[Nr]              PJ_ELEMENTARY .. PJ_CHEB
  *   reversible[Nr]        0/1; reverse rate from the equilibrium constant
  *   reac_sp/reac_nu[Nr*PJ_MAX_SP], prod_sp/prod_nu[...]: species (-1 pads)
  *                         and positive integer stoichiometric coefficients
@@ -94,6 +96,24 @@ typedef struct pj_mech pj_mech;
  *   sri[Nr*5]             a, b, c, d, e
  *   eff_ptr[Nr+1], eff_sp[], eff_val[]  non-default third-body efficiencies
  *                         (CSR by reaction; default efficiency is 1)
+ * Less common reaction types (Sec. 2.2 names them; standard forms).  Every
+ * pointer below may be NULL when no reaction uses it:
+ *   chem[Nr]              1: chemically-activated falloff (Lindemann / Troe /
+ *                         SRI kinds): rate k0 F / (1 + Pr) instead of
+ *                         k_inf F Pr / (1 + Pr)
+ *   rev_explicit[Nr], rev_A/rev_beta/rev_Ea[Nr]  1: reverse rate
+ *                         rev_A T^rev_beta exp(-rev_Ea/(R_cal T)) instead of
+ *                         k_f / K_c (reversible reactions)
+ *   plog_ptr[Nr+1], plog[n*4]  PJ_PLOG entries (P [Pa], A, beta, Ea), P
+ *                         strictly ascending: ln k is linear in ln P between
+ *                         neighbours, held at the end values outside
+ *   cheb_ptr[Nr+1], cheb_nT/cheb_nP[Nr], cheb_range[Nr*4] (T_min, T_max [K],
+ *                         P_min, P_max [Pa]), cheb_coef[] (row-major N_T x N_P
+ *                         per reaction): PJ_CHEB, log10 k = sum a_tp
+ *                         phi_t(T~) phi_p(P~), phi_n Chebyshev polynomials,
+ *                         T~ = (2/T - 1/T_min - 1/T_max)/(1/T_max - 1/T_min),
+ *                         P~ = (2 log P - log P_min - log P_max)/(log P_max
+ *                         - log P_min); N_T, N_P in 1..16
  */
 typedef struct {
   int32_t n_species, n_reactions;
@@ -119,6 +139,18 @@ typedef struct {
   const int32_t* eff_ptr;
   const int32_t* eff_sp;
   const double* eff_val;
+  const int32_t* chem;
+  const int32_t* rev_explicit;
+  const double* rev_A;
+  const double* rev_beta;
+  const double* rev_Ea;
+  const int32_t* plog_ptr;
+  const double* plog;
+  const int32_t* cheb_ptr;
+  const int32_t* cheb_nT;
+  const int32_t* cheb_nP;
+  const double* cheb_range;
+  const double* cheb_coef;
 } pj_mech_desc;
 
 /* Thread-local message describing the last error on this thread. */

@@ -13,6 +13,7 @@ from . import build as _build
 PJ_OK, PJ_ERR_ARG, PJ_ERR_MECH, PJ_ERR_CUDA, PJ_ERR_NOMEM, PJ_ERR_UNSUPPORTED, PJ_ERR_TIMEOUT = range(7)
 PJ_CONP, PJ_CONV = 0, 1
 PJ_CSR, PJ_CSC, PJ_DENSE = 0, 1, 2
+PJ_ELEMENTARY, PJ_THIRD_BODY, PJ_LINDEMANN, PJ_TROE, PJ_SRI, PJ_PLOG, PJ_CHEB = range(7)
 PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_LU = 0, 1, 2, 3, 4, 5, 6
 PJ_F64, PJ_F32 = 0, 1
 PJ_MAX_SP = 4
@@ -29,7 +30,10 @@ class pj_mech_desc(C.Structure):
                 ("kind", _ip), ("reversible", _ip), ("reac_sp", _ip), ("reac_nu", _ip),
                 ("prod_sp", _ip), ("prod_nu", _ip), ("A", _dp), ("beta", _dp), ("Ea", _dp),
                 ("A0", _dp), ("beta0", _dp), ("Ea0", _dp), ("troe", _dp), ("troe_n", _ip),
-                ("sri", _dp), ("eff_ptr", _ip), ("eff_sp", _ip), ("eff_val", _dp)]
+                ("sri", _dp), ("eff_ptr", _ip), ("eff_sp", _ip), ("eff_val", _dp),
+                ("chem", _ip), ("rev_explicit", _ip), ("rev_A", _dp), ("rev_beta", _dp), ("rev_Ea", _dp),
+                ("plog_ptr", _ip), ("plog", _dp), ("cheb_ptr", _ip), ("cheb_nT", _ip), ("cheb_nP", _ip),
+                ("cheb_range", _dp), ("cheb_coef", _dp)]
 
 
 class pj_batch(C.Structure):

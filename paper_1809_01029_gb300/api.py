@@ -124,6 +124,24 @@ def pj_mech_create(mech) -> Mechanism:
         troe_n=_i32(mech.troe_n), sri=_f64(mech.sri).reshape(-1), eff_ptr=_i32(mech.eff_ptr),
         eff_sp=_i32(mech.eff_sp) if len(mech.eff_sp) else np.zeros(1, np.int32),
         eff_val=_f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1))
+    # less common reaction types (optional fields of the description object)
+    z = lambda: np.zeros(nr)
+    chem = getattr(mech, "chem", None)
+    keep.update(
+        chem=_i32(np.zeros(nr) if chem is None else np.asarray(chem).astype(np.int32)),
+        rev_explicit=_i32(np.asarray(getattr(mech, "rev_explicit", z())).astype(np.int32)))
+    rev_arr = np.asarray(getattr(mech, "rev_arr", np.zeros((nr, 3))), dtype=float).reshape(nr, 3)
+    keep.update(rev_A=_f64(rev_arr[:, 0]), rev_beta=_f64(rev_arr[:, 1]), rev_Ea=_f64(rev_arr[:, 2]))
+    plog = np.asarray(getattr(mech, "plog", np.zeros((0, 4))), dtype=float).reshape(-1)
+    cheb = np.asarray(getattr(mech, "cheb_coef", np.zeros(0)), dtype=float).reshape(-1)
+    shape = np.asarray(getattr(mech, "cheb_shape", np.zeros((nr, 2))), dtype=np.int64).reshape(nr, 2)
+    keep.update(
+        plog_ptr=_i32(getattr(mech, "plog_ptr", np.zeros(nr + 1))),
+        plog=_f64(plog) if len(plog) else np.zeros(1),
+        cheb_ptr=_i32(getattr(mech, "cheb_ptr", np.zeros(nr + 1))),
+        cheb_nT=_i32(shape[:, 0]), cheb_nP=_i32(shape[:, 1]),
+        cheb_range=_f64(np.asarray(getattr(mech, "cheb_range", np.zeros((nr, 4))), dtype=float).reshape(-1)),
+        cheb_coef=_f64(cheb) if len(cheb) else np.zeros(1))
     d = N.pj_mech_desc()
     d.n_species, d.n_reactions = ns, nr
     for k, v in keep.items():

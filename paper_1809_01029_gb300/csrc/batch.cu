@@ -58,11 +58,11 @@ struct BatchDev {
 };
 
 // Persistent kernel: OP 0 = source terms, 1 = analytical Jacobian (FP64).
-template <int OP, int MODE, int FMT>
-__global__ void __launch_bounds__(128) k_batched(DevMech m, const BatchDev* __restrict__ batches,
-                                                 const int64_t* __restrict__ tile_start, int nb,
-                                                 unsigned long long* counter, int* status, double* ws,
-                                                 int64_t ws_stride) {
+template <int OP, int MODE, int FMT, bool SPECIAL>
+__global__ void __launch_bounds__(128, 4) k_batched(DevMech m, const BatchDev* __restrict__ batches,
+                                                    const int64_t* __restrict__ tile_start, int nb,
+                                                    unsigned long long* counter, int* status, double* ws,
+                                                    int64_t ws_stride) {
   PJ_DYN_SMEM;
   load_exp_table(m.exp_tab);
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,17 +93,17 @@ __global__ void __launch_bounds__(128) k_batched(DevMech m, const BatchDev* __re
     const int64_t s = (tile - __ldg(tile_start + lo)) * 32 + lane;
     if (s < B.n) {
       if (OP == 0)
-        source_state<MODE>(m, A, B.param, B.phi, B.ld, s, B.out, status);
+        source_state<MODE, SPECIAL>(m, A, B.param, B.phi, B.ld, s, B.out, status);
       else
-        jacobian_state<MODE, FMT, double, false>(m, A, B.param, B.phi, B.ld, s, B.out, B.dphi, status, nullptr,
-                                                 0.0);
+        jacobian_state<MODE, FMT, double, false, false, SPECIAL>(m, A, B.param, B.phi, B.ld, s, B.out, B.dphi,
+                                                                 status, nullptr, 0.0);
     }
   }
 }
 
 template <int OP, int MODE, int FMT>
 static int launch_group(const pj_plan* p, const pj_plan::Group& g, cudaStream_t st) {
-  auto kern = k_batched<OP, MODE, FMT>;
+  auto kern = p->mech->dm.nr_plain < p->mech->dm.nr ? k_batched<OP, MODE, FMT, true> : k_batched<OP, MODE, FMT, false>;
   cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(plan counter)");
   kern<<<p->grid, p->tpb, p->smem, st>>>(p->mech->dm, static_cast<const BatchDev*>(g.d_batches), g.d_tile_start,
@@ -113,8 +113,9 @@ static int launch_group(const pj_plan* p, const pj_plan::Group& g, cudaStream_t 
 }
 
 template <int OP, int MODE, int FMT>
-static int set_kernel_smem(size_t smem) {
-  return set_smem(k_batched<OP, MODE, FMT>, smem);
+static int set_kernel_smem(const DevMech& m, size_t smem) {
+  if (m.nr_plain < m.nr) return set_smem(k_batched<OP, MODE, FMT, true>, smem);
+  return set_smem(k_batched<OP, MODE, FMT, false>, smem);
 }
 
 // dispatch over (op, mode, fmt)
@@ -149,9 +150,10 @@ struct RunGroups {
 };
 
 struct SetSmem {
+  const DevMech& m;
   size_t smem;
   template <int OP, int MODE, int FMT>
-  int go() { return set_kernel_smem<OP, MODE, FMT>(smem); }
+  int go() { return set_kernel_smem<OP, MODE, FMT>(m, smem); }
 };
 
 static int plan_arrays(const pj_plan* p) { return p->op == 0 ? source_arrays() : jacobian_arrays(); }
@@ -179,7 +181,7 @@ static int plan_configure(pj_plan* p, int tpb, int bps, int use_smem) {
   p->grid = sm_count() * bps;
   p->smem = use_smem ? per_thread * tpb : 0;
   if (use_smem) {
-    int rc = dispatch(p->op, p->mode, p->fmt, SetSmem{p->smem});
+    int rc = dispatch(p->op, p->mode, p->fmt, SetSmem{p->mech->dm, p->smem});
     if (rc) return rc;
   } else {
     const size_t need = per_thread * (size_t)p->grid * tpb;

@@ -31,7 +31,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 #endif
 
 // Forward values y = (wdot_0 .. wdot_{Ns-1}, dT/dt): y[k*ld + s].
-template <int MODE>
+template <int MODE, bool SPECIAL>
 __global__ void __launch_bounds__(128) k_eval_y(DevMech m, int64_t n, const double* __restrict__ param,
                                                 const double* __restrict__ phi, int64_t ld, double* __restrict__ y,
                                                 int* status, double* ws, int64_t ws_stride) {
@@ -69,32 +69,41 @@ __global__ void __launch_bounds__(128) k_eval_y(DevMech m, int64_t n, const doub
     den *= RU;
     const double logPRT = m.log_pstd_over_r - lnT;
     double w_bath = 0.0;
-    for (int i = 0; i < m.nr; i++) {
+    // Plain reactions (the first m.nr_plain in kernel order) run through a
+    // body compiled without the special cases (chemically activated, explicit
+    // reverse, P-log, Chebyshev), the rest through the general one.
+    auto reaction = [&](int i, auto gen_tag) {
+      constexpr bool GEN = decltype(gen_tag)::value;
       const Rxn* __restrict__ r = m.rxn + i;
       const int kind = __ldg(&r->kind);
       const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod), rev = __ldg(&r->rev);
-      const double lnkf = fma(__ldg(&r->beta), lnT, __ldg(&r->lnA)) - __ldg(&r->theta) * invT;
+      double lnkinf, u0, u1, u2;
+      const double lnkf = ln_kf<false, GEN>(m, r, kind, lnT, invT, st.lnP, lnkinf, u0, u1, u2);
       double kf, kr;
-      rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+      rate_constants<GEN>(m, A, aG, r, rev, nre, npr, lnkf, logPRT, lnT, invT, kf, kr);
       double dmy[PJ_MAX_SP];
       const double Rf = side_rate<false>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dmy);
       const double Rr = rev ? side_rate<false>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dmy) : 0.0;
       double c = 1.0;
-      if (kind != PJ_ELEMENTARY) {
+      if (has_third_body(kind)) {
         const double M = third_body(m, A, aC, r, st.Ctot);
         if (kind == PJ_THIRD_BODY) {
           c = M;
         } else {
           const double lnk0 = fma(__ldg(&r->beta0), lnT, __ldg(&r->lnA0)) - __ldg(&r->theta0) * invT;
-          const double Pr = pj_exp(lnk0 - lnkf) * M;
+          const double Pr = pj_exp(lnk0 - lnkinf) * M;
           double d1, d2;
           const double F = falloff_F<false>(r, kind, T, invT, lnT, Pr, d1, d2);
-          c = Pr / (1.0 + Pr) * F;
+          c = ((GEN && __ldg(&r->chem)) ? 1.0 : Pr) / (1.0 + Pr) * F;
         }
       }
       const double q = c * (Rf - Rr);
       scatter_wdot(r, nre, npr, bath, q, wrow, ld, w_bath);
-    }
+    };
+    for (int i = 0; i < m.nr_plain; i++) reaction(i, BoolTag<false>{});
+    if (SPECIAL)
+      for (int i = m.nr_plain; i < m.nr; i++) reaction(i, BoolTag<true>{});
+
     double num = 0.0;
     for (int k = 0; k < ns; k++) {
       double cp, h, sr;
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(128) k_eval_y(DevMech m, int64_t n, const doub
 // VJP.  Warps walk the batch 32 states at a time so that the per-reaction
 // parameter gradients can be summed over the warp with shuffles.  The
 // forward values y are produced on the way (needed for dT/dt's direct terms).
-template <int MODE>
+template <int MODE, bool SPECIAL>
 __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double* __restrict__ param,
                                              const double* __restrict__ phi, int64_t ld,
                                              const double* __restrict__ u_wdot, const double* __restrict__ u_T,
@@ -156,6 +165,7 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
       st.P = 1e5;
       st.invT = 1e-3;
       st.lnT = log(1000.0);
+      st.lnP = log(1e5);
       st.Ctot = st.P / (RU * st.T);
       for (int k = 0; k < ns; k++) A.at(aC, k) = st.Ctot / ns;
     }
@@ -195,15 +205,18 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
     const double mR_calT = -1.0 / (R_CAL * T);
 
     double gT = 0.0, gS = 0.0, gB = 0.0, w_bath = 0.0;
-    for (int i = 0; i < nr; i++) {
+    // Plain reactions (the first m.nr_plain in kernel order) run through a
+    // body compiled without the special cases (chemically activated, explicit
+    // reverse, P-log, Chebyshev), the rest through the general one.
+    auto reaction = [&](int i, auto gen_tag) {
+      constexpr bool GEN = decltype(gen_tag)::value;
       const Rxn* __restrict__ r = m.rxn + i;
       const int kind = __ldg(&r->kind);
       const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod), rev = __ldg(&r->rev);
-      const double beta = __ldg(&r->beta), theta = __ldg(&r->theta);
-      const double lnkf = fma(beta, lnT, __ldg(&r->lnA)) - theta * invT;
-      const double dlnkf = fma(theta, invT2, beta * invT);
+      double lnkinf, dlnkf, dlnP, dlnkinf;
+      const double lnkf = ln_kf<true, GEN>(m, r, kind, lnT, invT, st.lnP, lnkinf, dlnkf, dlnP, dlnkinf);
       double kf, kr;
-      rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+      rate_constants<GEN>(m, A, aG, r, rev, nre, npr, lnkf, logPRT, lnT, invT, kf, kr);
       double dh = 0.0, du = 0.0;
 #pragma unroll
       for (int a = 0; a < PJ_MAX_SP; a++) {
@@ -225,12 +238,17 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
       double Rr = 0.0, dlnkr = 0.0;
       if (rev) {
         Rr = side_rate<true>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dRr);
-        dlnkr = dlnkf - (dh - __ldg(&r->dnu)) * invT;
+        if (GEN && rev == 2)
+          dlnkr = fma(__ldg(m.tab + __ldg(&r->tab_lo) + 2), invT2, __ldg(m.tab + __ldg(&r->tab_lo) + 1) * invT);
+        else
+          dlnkr = dlnkf - (dh - __ldg(&r->dnu)) * invT;
       }
       const double Rn = Rf - Rr;
-      double c = 1.0, dcdT = 0.0, dcdS = 0.0, dcdM = 0.0, Q;
-      bool fall = false;
-      if (kind != PJ_ELEMENTARY) {
+      double c = 1.0, dcdT = 0.0, dcdS = 0.0, dcdM = 0.0;
+      // d q / d ln k_inf (k_inf: the Arrhenius set the parameter gradient is
+      // taken for) = part through the base rate + part through Pr
+      double Qpr = 0.0;
+      if (has_third_body(kind)) {
         const double M = third_body(m, A, aC, r, Ctot);
         const double ab = __ldg(&r->alpha_bath);
         const double dMdT = ab * dCb_T;
@@ -241,28 +259,36 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
           dcdT = dMdT;
           dcdS = dMdS;
         } else {
-          fall = true;
           const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
           const double lnk0 = fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
           const double dlnk0 = fma(theta0, invT2, beta0 * invT);
-          const double rk = pj_exp(lnk0 - lnkf);
+          const double rk = pj_exp(lnk0 - lnkinf);
           const double Pr = rk * M;
           double FxPr, FT;
           const double F = falloff_F<true>(r, kind, T, invT, lnT, Pr, FxPr, FT);
           const double i1p = 1.0 / (1.0 + Pr);
-          const double fr = Pr * i1p;
-          c = fr * F;
-          const double cPr = F * i1p * i1p + FxPr * i1p;
-          const double dPrdT = Pr * (dlnk0 - dlnkf) + rk * dMdT;
-          dcdT = fr * FT + cPr * dPrdT;
+          const double dPrdT = Pr * (dlnk0 - dlnkinf) + rk * dMdT;
+          double cPr;
+          if (GEN && __ldg(&r->chem)) {
+            c = F * i1p;
+            cPr = i1p * (FxPr / Pr - F * i1p);
+            dcdT = i1p * FT + cPr * dPrdT;
+          } else {
+            const double fr = Pr * i1p;
+            c = fr * F;
+            cPr = F * i1p * i1p + FxPr * i1p;
+            dcdT = fr * FT + cPr * dPrdT;
+          }
           dcdM = cPr * rk;
           dcdS = dcdM * dMdS;
-          // k_inf scales R and divides Pr: dq/d ln k_inf = c R - R Pr dc/dPr
-          Q = Rn * (c - cPr * Pr);
+          Qpr = -Rn * cPr * Pr;  // k_inf divides Pr
         }
       }
       const double q = c * Rn;
-      if (!fall) Q = q;
+      // the base rate is k_inf unless the reaction is chemically activated or
+      // pressure-dependent; with an explicit reverse rate only R' scales
+      const bool base_inf = !GEN || (kind < PJ_PLOG && !__ldg(&r->chem));
+      const double Q = (base_inf ? c * ((GEN && rev == 2) ? Rf : Rn) : 0.0) + Qpr;
       if (ok) scatter_wdot(r, nre, npr, bath, q, wrow, ld, w_bath);
       double dRdT = Rf * dlnkf - Rr * dlnkr;
       double dRdS = 0.0;
@@ -286,6 +312,11 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
             dRdS = fma(dRr[a], A.at(aC, k) * invV, dRdS);
           }
         }
+      }
+      if (GEN && MODE == PJ_CONV && kind >= PJ_PLOG) {
+        // P-log / Chebyshev rates depend on P = S; an explicit reverse rate does not
+        const double dP = dlnP / P;
+        dRdS = fma(Rf, dP, dRdS) - (rev == 1 ? Rr * dP : 0.0);
       }
       const double dqdT = fma(c, dRdT, Rn * dcdT);
       const double dqdS = fma(c, dRdS, Rn * dcdS);
@@ -312,7 +343,7 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
           else if (ok) red_add(grow + (int64_t)j * ld, ubV * val);
         }
       }
-      if (kind != PJ_ELEMENTARY) {
+      if (has_third_body(kind)) {
         const double t = Rn * dcdM;
         for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++) {
           const int j = __ldg(m.eff_sp + e);
@@ -334,7 +365,11 @@ __global__ void __launch_bounds__(128) k_vjp(DevMech m, int64_t n, const double*
         red_add(my_part + 3 * i + 1, s1);
         red_add(my_part + 3 * i + 2, s2);
       }
-    }
+    };
+    for (int i = 0; i < m.nr_plain; i++) reaction(i, BoolTag<false>{});
+    if (SPECIAL)
+      for (int i = m.nr_plain; i < nr; i++) reaction(i, BoolTag<true>{});
+
     if (!ok) continue;
 
     // y, and the direct dependence of dT/dt on the state through E_k(T), D
@@ -436,14 +471,12 @@ int launch_eval_y(const DevMech& m, int mode, int64_t n, const double* param, co
   if (p.global_ws && (!work || work_bytes < p.ws_bytes))
     return fail(PJ_ERR_NOMEM, "workspace too small for pj_eval_y (see pj_workspace_size)");
   double* ws = p.global_ws ? static_cast<double*>(work) : nullptr;
+  const bool special = m.nr_plain < m.nr;
+  auto kern = mode == PJ_CONP ? (special ? k_eval_y<PJ_CONP, true> : k_eval_y<PJ_CONP, false>)
+                              : (special ? k_eval_y<PJ_CONV, true> : k_eval_y<PJ_CONV, false>);
   int rc;
-  if (mode == PJ_CONP) {
-    if ((rc = set_smem(k_eval_y<PJ_CONP>, p.smem))) return rc;
-    k_eval_y<PJ_CONP><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, y, status, ws, p.ws_stride);
-  } else {
-    if ((rc = set_smem(k_eval_y<PJ_CONV>, p.smem))) return rc;
-    k_eval_y<PJ_CONV><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, y, status, ws, p.ws_stride);
-  }
+  if ((rc = set_smem(kern, p.smem))) return rc;
+  kern<<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, y, status, ws, p.ws_stride);
   return check_cuda(cudaGetLastError(), "k_eval_y launch");
 }
 
@@ -458,16 +491,12 @@ int launch_vjp(const DevMech& m, int mode, int64_t n, const double* param, const
   double* part = reinterpret_cast<double*>(static_cast<char*>(work) + align256(p.ws_bytes));
   cudaError_t e = cudaMemsetAsync(part, 0, p.part_bytes, st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(vjp partials)");
+  const bool special = m.nr_plain < m.nr;
+  auto kern = mode == PJ_CONP ? (special ? k_vjp<PJ_CONP, true> : k_vjp<PJ_CONP, false>)
+                              : (special ? k_vjp<PJ_CONV, true> : k_vjp<PJ_CONV, false>);
   int rc;
-  if (mode == PJ_CONP) {
-    if ((rc = set_smem(k_vjp<PJ_CONP>, p.smem))) return rc;
-    k_vjp<PJ_CONP><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, u_wdot, u_T, y, g_phi, part, status, ws,
-                                                  p.ws_stride);
-  } else {
-    if ((rc = set_smem(k_vjp<PJ_CONV>, p.smem))) return rc;
-    k_vjp<PJ_CONV><<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, u_wdot, u_T, y, g_phi, part, status, ws,
-                                                  p.ws_stride);
-  }
+  if ((rc = set_smem(kern, p.smem))) return rc;
+  kern<<<p.grid, p.tpb, p.smem, st>>>(m, n, param, phi, ld, u_wdot, u_T, y, g_phi, part, status, ws, p.ws_stride);
   if ((rc = check_cuda(cudaGetLastError(), "k_vjp launch"))) return rc;
   const int64_t nt = (int64_t)m.nr * 3;
   if (nt > 0) {

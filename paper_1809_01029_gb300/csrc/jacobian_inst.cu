@@ -27,14 +27,16 @@ using InstPlan = LaunchPlan;
 template <int MODE, int FMT>
 static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double* ws,
                        cudaStream_t st) {
-  return launch_jac_t<MODE, FMT, InstDT, kInstNewton>(m, p, n, a, ws, st);
+  if (m.nr_plain < m.nr) return launch_jac_t<MODE, FMT, InstDT, kInstNewton, true>(m, p, n, a, ws, st);
+  return launch_jac_t<MODE, FMT, InstDT, kInstNewton, false>(m, p, n, a, ws, st);
 }
 #else
 using InstPlan = TmPlan;
 template <int MODE, int FMT>
 static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double* ws,
                        cudaStream_t st) {
-  return launch_jac_tm_s<MODE, FMT, InstDT, kInstNewton, PJ_INST_TM>(m, p, n, a, ws, st);
+  if (m.nr_plain < m.nr) return launch_jac_tm_s<MODE, FMT, InstDT, kInstNewton, PJ_INST_TM, true>(m, p, n, a, ws, st);
+  return launch_jac_tm_s<MODE, FMT, InstDT, kInstNewton, PJ_INST_TM, false>(m, p, n, a, ws, st);
 }
 #endif
 

@@ -14,7 +14,7 @@
 
 namespace pj {
 
-template <int MODE, int FMT, typename DT, bool NEWTON>
+template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL>
 __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const double* __restrict__ param,
                                                   const double* __restrict__ phi, int64_t ld,
                                                   DT* __restrict__ J, double* __restrict__ dphi,
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
     A.stride = blockDim.x;
   }
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x)
-    jacobian_state<MODE, FMT, DT, NEWTON>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma);
+    jacobian_state<MODE, FMT, DT, NEWTON, false, SPECIAL>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma);
 }
 
 // Jacobian with h_k/RT in tensor memory: blocks of 128 threads (one warp per
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
 // columns before exiting.  C_k and g_k/RT are the state arrays 0 and 1: the
 // first SPLIT of them sit in shared memory, the rest in a global workspace
 // of ws_stride threads (the grid then covers exactly ws_stride threads).
-template <int MODE, int FMT, typename DT, bool NEWTON, int SPLIT>
+template <int MODE, int FMT, typename DT, bool NEWTON, int SPLIT, bool SPECIAL>
 __global__ void __launch_bounds__(128) k_jacobian_tm(DevMech m, int64_t n, const double* __restrict__ param,
                                                      const double* __restrict__ phi, int64_t ld,
                                                      DT* __restrict__ J, double* __restrict__ dphi, int* status,
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) k_jacobian_tm(DevMech m, int64_t n, const
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < n; base += stride) {
     const int64_t s = base + lane;
-    jacobian_state<MODE, FMT, DT, NEWTON, true>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma, tm_row,
+    jacobian_state<MODE, FMT, DT, NEWTON, true, SPECIAL>(m, A, param, phi, ld, s, J, dphi, status, hstep, gamma, tm_row,
                                                 s < n);
   }
   tmem_fence_before();
@@ -92,10 +92,10 @@ static size_t tm_smem_cap_ctas(K kern, size_t dyn, int ctas) {
   return pad > dyn ? pad : dyn;
 }
 
-template <int MODE, int FMT, typename DT, bool NEWTON, int SPLIT>
+template <int MODE, int FMT, typename DT, bool NEWTON, int SPLIT, bool SPECIAL>
 static int launch_jac_tm_s(const DevMech& m, const TmPlan& t, int64_t n, const JacArgs& a, double* ws,
                            cudaStream_t st) {
-  auto kern = k_jacobian_tm<MODE, FMT, DT, NEWTON, SPLIT>;
+  auto kern = k_jacobian_tm<MODE, FMT, DT, NEWTON, SPLIT, SPECIAL>;
   int rc;
   if ((rc = set_smem(kern, t.smem))) return rc;
   const size_t smem = tm_smem_cap_ctas(kern, t.smem, t.ctas);
@@ -112,10 +112,10 @@ static int launch_jac_tm_s(const DevMech& m, const TmPlan& t, int64_t n, const J
   return check_cuda(cudaGetLastError(), "k_jacobian_tm launch");
 }
 
-template <int MODE, int FMT, typename DT, bool NEWTON>
+template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL>
 static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const JacArgs& a, double* ws,
                         cudaStream_t st) {
-  auto kern = k_jacobian<MODE, FMT, DT, NEWTON>;
+  auto kern = k_jacobian<MODE, FMT, DT, NEWTON, SPECIAL>;
   int rc;
   if ((rc = set_smem(kern, p.smem))) return rc;
   const LaunchPlan q = resident_grid(kern, p);

@@ -40,7 +40,7 @@ namespace pj {
 // ---------------------------------------------------------------------------
 // Shared memory holds C_k and g_k/RT per state; production rates are summed
 // by L2 reductions into the output rows (the bath gas in a register).
-template <int MODE>
+template <int MODE, bool SPECIAL>
 __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, const double* __restrict__ param,
                                                       const double* __restrict__ phi, int64_t ld,
                                                       double* __restrict__ out, int* status, double* ws,
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_source_terms(DevMech m, int64_t n, cons
     A.stride = blockDim.x;
   }
   for (int64_t s = gtid; s < n; s += (int64_t)gridDim.x * blockDim.x)
-    source_state<MODE>(m, A, param, phi, ld, s, out, status);
+    source_state<MODE, SPECIAL>(m, A, param, phi, ld, s, out, status);
 }
 
 // pj_exp next to the library exp, for verification (pj_diag_exp).
@@ -138,7 +138,9 @@ int launch_source(const DevMech& m, int mode, int64_t n, const double* param, co
     return fail(PJ_ERR_NOMEM, "workspace too small for the source-term kernel (see pj_workspace_size)");
   double* ws = p.global_ws ? static_cast<double*>(work) : nullptr;
   int rc;
-  auto kern = mode == PJ_CONP ? k_source_terms<PJ_CONP> : k_source_terms<PJ_CONV>;
+  const bool special = m.nr_plain < m.nr;
+  auto kern = mode == PJ_CONP ? (special ? k_source_terms<PJ_CONP, true> : k_source_terms<PJ_CONP, false>)
+                              : (special ? k_source_terms<PJ_CONV, true> : k_source_terms<PJ_CONV, false>);
   if ((rc = set_smem(kern, p.smem))) return rc;
   const LaunchPlan q = resident_grid(kern, p);
   kern<<<q.grid, q.tpb, q.smem, st>>>(m, n, param, phi, ld, out, status, ws, q.ws_stride);

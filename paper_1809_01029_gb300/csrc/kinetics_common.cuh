@@ -15,7 +15,10 @@ namespace pj {
 
 struct StateScalars {
   double T, V, P, invT, lnT, Ctot;
+  double lnP;  // ln P [Pa], formed only when some reaction depends on pressure
 };
+
+__device__ __forceinline__ bool has_third_body(int kind) { return kind >= PJ_THIRD_BODY && kind <= PJ_SRI; }
 
 // Load one state, fill C_k (k < Ns-1 as n_k/V; the bath gas as C_tot minus
 // the others summed in species order) and check validity.
@@ -35,6 +38,7 @@ __device__ __forceinline__ bool load_state(const DevMech& m, const double* __res
     acc += c;
   }
   const double Ctot = P / (RU * T);
+  st.lnP = m.has_pdep ? log(P) : 0.0;
   const double Cns = Ctot - acc;
   A.at(aC, ns - 1) = Cns;
   ok = ok && isfinite(acc) && isfinite(Cns) && !(Cns < -1e-12 * Ctot);
@@ -197,13 +201,126 @@ __device__ __forceinline__ double side_rate(const SA& A, int aC, const Rxn* __re
   }
 }
 
+// ln k of a P-log or Chebyshev reaction and, with DER, d ln k / dT and
+// d ln k / d ln P.  P-log: Arrhenius rates at ascending ln P_m (table rows
+// ln P, ln A, beta, theta), ln k linear in ln P on [ln P_m, ln P_m+1), held at
+// the end values below the first and from the last pressure on.  Chebyshev:
+// ln k = sum_t sum_p (ln10 a_tp) phi_t(T~) phi_p(P~) with T~ = cT1/T + cT0,
+// P~ = cP1 ln P + cP0 and phi_n the Chebyshev polynomials (three-term
+// recurrence, which also extends them outside [-1, 1]).
+// Not inlined: it runs only for pressure-dependent reactions, and keeping it
+// out of the reaction loop keeps that loop's register allocation unchanged.
+template <bool DER>
+__device__ __noinline__ double lnk_pdep(const DevMech& m, const Rxn* __restrict__ r, int kind, double lnT,
+                                        double invT, double lnP, double& d_T, double& d_lnP) {
+  const double* __restrict__ t = m.tab + __ldg(&r->tab_lo) + (__ldg(&r->rev) == 2 ? 3 : 0);
+  if (kind == PJ_PLOG) {
+    const int n = __ldg(&r->tab_n);
+    auto lnk_at = [&](int j) { return fma(__ldg(t + 4 * j + 2), lnT, __ldg(t + 4 * j + 1)) - __ldg(t + 4 * j + 3) * invT; };
+    auto dT_at = [&](int j) { return fma(__ldg(t + 4 * j + 3), invT * invT, __ldg(t + 4 * j + 2) * invT); };
+    if (lnP < __ldg(t) || n == 1) {
+      if (DER) { d_T = dT_at(0); d_lnP = 0.0; }
+      return lnk_at(0);
+    }
+    if (lnP >= __ldg(t + 4 * (n - 1))) {
+      if (DER) { d_T = dT_at(n - 1); d_lnP = 0.0; }
+      return lnk_at(n - 1);
+    }
+    int j = 0;
+    while (j + 2 < n && lnP >= __ldg(t + 4 * (j + 1))) j++;
+    const double p0 = __ldg(t + 4 * j), p1 = __ldg(t + 4 * (j + 1));
+    const double k0 = lnk_at(j), k1 = lnk_at(j + 1);
+    const double slope = (k1 - k0) / (p1 - p0);
+    if (DER) {
+      const double w = (lnP - p0) / (p1 - p0);
+      d_T = fma(w, dT_at(j + 1) - dT_at(j), dT_at(j));
+      d_lnP = slope;
+    }
+    return fma(slope, lnP - p0, k0);
+  }
+  // Chebyshev
+  const int nT = __ldg(&r->tab_n), nP = __ldg(&r->tab_m);
+  const double x = fma(__ldg(t), invT, __ldg(t + 1));
+  const double y = fma(__ldg(t + 2), lnP, __ldg(t + 3));
+  const double* __restrict__ a = t + 4;
+  double S = 0.0, Sx = 0.0, Sy = 0.0;
+  double pt0 = 1.0, pt1 = x, dt0 = 0.0, dt1 = 1.0;  // phi_t(x) and phi_t'(x)
+  for (int it = 0; it < nT; it++) {
+    const double pt = it == 0 ? 1.0 : pt1, dpt = it == 0 ? 0.0 : dt1;
+    double B = 0.0, By = 0.0;
+    double pp0 = 1.0, pp1 = y, dp0 = 0.0, dp1 = 1.0;
+    for (int ip = 0; ip < nP; ip++) {
+      const double pp = ip == 0 ? 1.0 : pp1, dpp = ip == 0 ? 0.0 : dp1;
+      const double c = __ldg(a + it * nP + ip);
+      B = fma(c, pp, B);
+      if (DER) By = fma(c, dpp, By);
+      if (ip >= 1) {
+        const double pn = fma(2.0 * y, pp1, -pp0), dn = fma(2.0 * y, dp1, fma(2.0, pp1, -dp0));
+        pp0 = pp1; pp1 = pn; dp0 = dp1; dp1 = dn;
+      }
+    }
+    S = fma(pt, B, S);
+    if (DER) {
+      Sx = fma(dpt, B, Sx);
+      Sy = fma(pt, By, Sy);
+    }
+    if (it >= 1) {
+      const double pn = fma(2.0 * x, pt1, -pt0), dn = fma(2.0 * x, dt1, fma(2.0, pt1, -dt0));
+      pt0 = pt1; pt1 = pn; dt0 = dt1; dt1 = dn;
+    }
+  }
+  if (DER) {
+    d_T = -Sx * __ldg(t) * invT * invT;
+    d_lnP = Sy * __ldg(t + 2);
+  }
+  return S;
+}
+
+// ln of reaction r's forward rate constant: the Arrhenius set for
+// elementary, third-body and falloff reactions, the low-pressure set for
+// chemically-activated ones, the P-log / Chebyshev forms otherwise.  lnkinf
+// is the Arrhenius set itself (the high-pressure limit in Pr).  With DER:
+// d_T, d_lnP of ln k_f and dinf_T of ln k_inf.
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
+template <bool DER, bool GEN = true>
+__device__ __forceinline__ double ln_kf(const DevMech& m, const Rxn* __restrict__ r, int kind, double lnT,
+                                        double invT, double lnP, double& lnkinf, double& d_T, double& d_lnP,
+                                        double& dinf_T) {
+  const double beta = __ldg(&r->beta), theta = __ldg(&r->theta);
+  lnkinf = fma(beta, lnT, __ldg(&r->lnA)) - theta * invT;
+  if (DER) {
+    dinf_T = fma(theta, invT * invT, beta * invT);
+    d_T = dinf_T;
+    d_lnP = 0.0;
+  }
+  if (!GEN) return lnkinf;  // plain reactions: the Arrhenius set
+  if (kind >= PJ_PLOG) return lnk_pdep<DER>(m, r, kind, lnT, invT, lnP, d_T, d_lnP);
+  if (__ldg(&r->chem)) {
+    const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
+    if (DER) d_T = fma(theta0, invT * invT, beta0 * invT);
+    return fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
+  }
+  return lnkinf;
+}
+
 // Forward and reverse rate constants; the two exponentials sit in one basic
-// block so their dependency chains interleave.
-template <class SA>
-__device__ __forceinline__ void rate_constants(const SA& A, int aG, const Rxn* __restrict__ r, int rev,
-                                               int nre, int npr, double lnkf, double logPRT, double& kf,
-                                               double& kr) {
-  if (rev) {
+// block so their dependency chains interleave.  rev == 2: explicit reverse
+// Arrhenius set instead of k_f / K_c.
+template <bool GEN = true, class SA>
+__device__ __forceinline__ void rate_constants(const DevMech& m, const SA& A, int aG, const Rxn* __restrict__ r,
+                                               int rev,
+                                               int nre, int npr, double lnkf, double logPRT, double lnT,
+                                               double invT, double& kf, double& kr) {
+  if (GEN && rev == 2) {
+    const double* __restrict__ rt = m.tab + __ldg(&r->tab_lo);
+    const double larg = fma(__ldg(rt + 1), lnT, __ldg(rt)) - __ldg(rt + 2) * invT;
+    kf = pj_exp(lnkf);
+    kr = pj_exp(larg);
+  } else if (rev) {
     double dg = 0.0;
 #pragma unroll
     for (int a = 0; a < PJ_MAX_SP; a++) {

@@ -8,7 +8,7 @@
 namespace pj {
 
 // One state of the source-term evaluation (s < n, arrays A of this thread).
-template <int MODE, class SA>
+template <int MODE, bool SPECIAL = true, class SA>
 __device__ __forceinline__ void source_state(const DevMech& m, const SA& A, const double* __restrict__ param,
                                              const double* __restrict__ phi, int64_t ld, int64_t s,
                                              double* __restrict__ out, int* status) {
@@ -34,27 +34,35 @@ __device__ __forceinline__ void source_state(const DevMech& m, const SA& A, cons
   const double logPRT = m.log_pstd_over_r - lnT;  // ln(P_std / (R T))
   double w_bath = 0.0;
 
-  for (int i = 0; i < m.nr; i++) {
+  // Plain reactions (the first m.nr_plain in kernel order) run through a
+  // body compiled without the special cases (chemically activated, explicit
+  // reverse, P-log, Chebyshev), the rest through the general one; kernels for
+  // mechanisms without special reactions are instantiated with SPECIAL =
+  // false and carry no general body at all.
+  auto reaction = [&](int i, auto gen_tag) {
+    constexpr bool GEN = decltype(gen_tag)::value;
     const Rxn* __restrict__ r = m.rxn + i;
     const int kind = __ldg(&r->kind);
     const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod), rev = __ldg(&r->rev);
-    const double lnkf = fma(__ldg(&r->beta), lnT, __ldg(&r->lnA)) - __ldg(&r->theta) * invT;
+    double lnkinf, u0, u1, u2;
+    const double lnkf = ln_kf<false, GEN>(m, r, kind, lnT, invT, st.lnP, lnkinf, u0, u1, u2);
     double kf, kr;
-    rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+    rate_constants<GEN>(m, A, aG, r, rev, nre, npr, lnkf, logPRT, lnT, invT, kf, kr);
     double dmy[PJ_MAX_SP];
     const double Rf = side_rate<false>(A, aC, r, 0, __ldg(&r->shape[0]), nre, kf, dmy);
     const double Rr = rev ? side_rate<false>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dmy) : 0.0;
     double c = 1.0;
-    if (kind != PJ_ELEMENTARY) {
+    if (has_third_body(kind)) {
       const double M = third_body(m, A, aC, r, st.Ctot);
       if (kind == PJ_THIRD_BODY) {
         c = M;
       } else {
         const double lnk0 = fma(__ldg(&r->beta0), lnT, __ldg(&r->lnA0)) - __ldg(&r->theta0) * invT;
-        const double Pr = pj_exp(lnk0 - lnkf) * M;
+        const double Pr = pj_exp(lnk0 - lnkinf) * M;
         double d1, d2;
         const double F = falloff_F<false>(r, kind, T, invT, lnT, Pr, d1, d2);
-        c = Pr / (1.0 + Pr) * F;
+        // falloff: k_inf Pr/(1+Pr) F; chemically activated: k0 F/(1+Pr)
+        c = ((GEN && __ldg(&r->chem)) ? 1.0 : Pr) / (1.0 + Pr) * F;
       }
     }
     const double q = c * (Rf - Rr);
@@ -73,7 +81,11 @@ __device__ __forceinline__ void source_state(const DevMech& m, const SA& A, cons
         else red_add(wrow + (int64_t)k * ld, v);
       }
     }
-  }
+  };
+  for (int i = 0; i < m.nr_plain; i++) reaction(i, BoolTag<false>{});
+  if (SPECIAL)
+    for (int i = m.nr_plain; i < m.nr; i++) reaction(i, BoolTag<true>{});
+
 
   // energy equation and ideal-gas state equation
   double num = 0.0, Om = 0.0;
@@ -139,7 +151,8 @@ __device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
 // TMEM accesses are warp-collective): a lane past the batch (act = false) or
 // with an invalid state computes on a harmless dummy state with every global
 // read and write of the batch masked.
-template <int MODE, int FMT, typename DT, bool NEWTON, bool TM = false, class SA = StateArrays>
+template <int MODE, int FMT, typename DT, bool NEWTON, bool TM = false, bool SPECIAL = true,
+          class SA = StateArrays>
 __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
                                                const double* __restrict__ param, const double* __restrict__ phi,
                                                int64_t ld, int64_t s, DT* __restrict__ J, double* __restrict__ dphi,
@@ -163,6 +176,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
     st.P = 1e5;
     st.invT = 1e-3;
     st.lnT = log(1000.0);
+    st.lnP = log(1e5);
     st.Ctot = st.P / (RU * st.T);
     for (int k = 0; k < ns; k++) A.at(aC, k) = st.Ctot / ns;
   }
@@ -213,16 +227,22 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
   DT AT_T = 0, AT_S = 0, AS_T = 0, AS_S = 0, ATB = 0, ASB = 0;
   double w_bath = 0;
 
-  for (int i = 0; i < m.nr; i++) {
+  // Plain reactions (the first m.nr_plain in kernel order) run through a
+  // body compiled without the special cases (chemically activated, explicit
+  // reverse, P-log, Chebyshev), the rest through the general one; kernels for
+  // mechanisms without special reactions are instantiated with SPECIAL =
+  // false and carry no general body at all.
+  auto reaction = [&](int i, auto gen_tag) {
+    constexpr bool GEN = decltype(gen_tag)::value;
     const Rxn* __restrict__ r = m.rxn + i;
     const int kind = __ldg(&r->kind);
     const int nre = __ldg(&r->nreac), npr = __ldg(&r->nprod);
     const int rev = __ldg(&r->rev);
-    const double beta = __ldg(&r->beta), theta = __ldg(&r->theta);
-    const double lnkf = fma(beta, lnT, __ldg(&r->lnA)) - theta * invT;
-    const DT dlnkf = DT(theta) * invT2_t + DT(beta) * invT_t;
+    double lnkinf, dlnkf_d, dlnP_d, dlnkinf_d;
+    const double lnkf = ln_kf<true, GEN>(m, r, kind, lnT, invT, st.lnP, lnkinf, dlnkf_d, dlnP_d, dlnkinf_d);
+    const DT dlnkf = DT(dlnkf_d), dlnkinf = DT(dlnkinf_d);
     double kf, kr;
-    rate_constants(A, aG, r, rev, nre, npr, lnkf, logPRT, kf, kr);
+    rate_constants<GEN>(m, A, aG, r, rev, nre, npr, lnkf, logPRT, lnT, invT, kf, kr);
     double dh = 0.0;
     if (TM) __syncwarp();
 #pragma unroll
@@ -236,7 +256,10 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
     DT dlnkr = DT(0);
     if (rev) {
       Rr = side_rate<true>(A, aC, r, PJ_MAX_SP, __ldg(&r->shape[1]), npr, kr, dRr);
-      dlnkr = dlnkf - DT(dh - __ldg(&r->dnu)) * invT_t;
+      if (GEN && rev == 2)
+        dlnkr = DT(fma(__ldg(m.tab + __ldg(&r->tab_lo) + 2), invT2, __ldg(m.tab + __ldg(&r->tab_lo) + 1) * invT));
+      else
+        dlnkr = dlnkf - DT(dh - __ldg(&r->dnu)) * invT_t;
     }
     const double Rn = Rf - Rr;
     const DT Rn_t = DT(Rn);
@@ -244,7 +267,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
     // pressure modification c (FP64) and its derivatives (DT)
     double c = 1.0;
     DT dcdT = 0, dcdS = 0, dcdM = 0;
-    if (kind != PJ_ELEMENTARY) {
+    if (has_third_body(kind)) {
       const double M = third_body(m, A, aC, r, Ctot);
       const DT ab = DT(__ldg(&r->alpha_bath));
       const DT dMdT = ab * dCb_T_t;
@@ -257,20 +280,34 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
       } else {
         const double beta0 = __ldg(&r->beta0), theta0 = __ldg(&r->theta0);
         const double lnk0 = fma(beta0, lnT, __ldg(&r->lnA0)) - theta0 * invT;
-        const DT dlnk0 = DT(theta0) * invT2_t + DT(beta0) * invT_t;
-        const double rk = pj_exp(lnk0 - lnkf);
+        const double dlnk0 = fma(theta0, invT2, beta0 * invT);
+        // per-reaction scalars of the blending function, in FP64 whatever DT
+        // (its derivative can subtract terms of similar size)
+        const double rk = pj_exp(lnk0 - lnkinf);
         const double Pr = rk * M;
-        DT FxPr, FT;
-        const double F = falloff_F<true, DT>(r, kind, T, invT, lnT, Pr, FxPr, FT);
+        double FxPr, FT;
+        const double F = falloff_F<true, double>(r, kind, T, invT, lnT, Pr, FxPr, FT);
         const double i1p = 1.0 / (1.0 + Pr);
-        const double fr = Pr * i1p;
-        c = fr * F;
-        const DT i1p_t = DT(i1p), F_t = DT(F), Pr_t = DT(Pr), rk_t = DT(rk);
-        const DT cPr = F_t * i1p_t * i1p_t + FxPr * i1p_t;
-        const DT dPrdT = Pr_t * (dlnk0 - dlnkf) + rk_t * dMdT;
-        dcdT = DT(fr) * FT + cPr * dPrdT;
-        dcdM = cPr * rk_t;
-        dcdS = dcdM * dMdS;
+        const double ab_d = __ldg(&r->alpha_bath);
+        const double dMdT_d = ab_d * dCb_T;
+        const double dMdS_d = MODE == PJ_CONP ? (ab_d * Ctot - M) * invV : ab_d * Ctot / P;
+        const double dPrdT = Pr * (dlnk0 - dlnkinf_d) + rk * dMdT_d;
+        double cPr, dcdT_d;
+        if (GEN && __ldg(&r->chem)) {
+          // c = F / (1 + Pr): dc/dPr = (dF/dPr) / (1 + Pr) - F / (1 + Pr)^2
+          c = F * i1p;
+          cPr = i1p * (FxPr / Pr - F * i1p);
+          dcdT_d = i1p * FT + cPr * dPrdT;
+        } else {
+          // c = F Pr / (1 + Pr)
+          const double fr = Pr * i1p;
+          c = fr * F;
+          cPr = F * i1p * i1p + FxPr * i1p;
+          dcdT_d = fr * FT + cPr * dPrdT;
+        }
+        dcdT = DT(dcdT_d);
+        dcdM = DT(cPr * rk);
+        dcdS = DT(cPr * rk * dMdS_d);
       }
     }
     const DT c_t = DT(c);
@@ -305,6 +342,12 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
           dRdS = dRdS + dRr_t[a] * (DT(A.at(aC, k)) * invV_t);
         }
       }
+    }
+    if (GEN && MODE == PJ_CONV && kind >= PJ_PLOG) {
+      // P-log / Chebyshev rates depend on P = S (held fixed in CONP); an
+      // explicit reverse rate does not
+      const DT dP = DT(dlnP_d / P);
+      dRdS = dRdS + DT(Rf) * dP - (rev == 1 ? DT(Rr) * dP : DT(0));
     }
     const double q = c * Rn;
     const DT dqdT = c_t * dRdT + Rn_t * dcdT;
@@ -360,7 +403,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
       if (a < nre) slot(__ldg(&r->sp[a]), c_t * dRf_t[a]);
       if (rev && a < npr) slot(__ldg(&r->sp[PJ_MAX_SP + a]), dneg(c_t * dRr_t[a]));
     }
-    if (kind != PJ_ELEMENTARY) {
+    if (has_third_body(kind)) {
       const DT t = Rn_t * dcdM;
       for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
         slot(__ldg(m.eff_sp + e), t * DT(__ldg(m.eff_am1 + e)));
@@ -374,7 +417,10 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
       ATB = ATB + dE * Bi;
       ASB = ASB + dW * Bi;
     }
-  }
+  };
+  for (int i = 0; i < m.nr_plain; i++) reaction(i, BoolTag<false>{});
+  if (SPECIAL)
+    for (int i = m.nr_plain; i < m.nr; i++) reaction(i, BoolTag<true>{});
 
   // source terms; the G array now holds Cx_k = R (cp_k or cv_k)
   if (TM) __syncwarp();
@@ -405,7 +451,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
   // energy row 0 and state row 1
   const DT iden = DT(1.0 / den);
   const DT Tdot_t = DT(Tdot), Om_t = DT(Om);
-  const DT Cx_b = DT(A.at(aG, bath));
+  const double Cx_b = A.at(aG, bath);  // differences Cx_j - Cx_b are formed in FP64 (they can cancel)
   const DT rtvp = DT(MODE == PJ_CONP ? RU * T * V / P : RU * T);
   for (int j = 0; j < N; j++) {
     const int64_t e0 = jpos<FMT>(m, 0, j), e1 = jpos<FMT>(m, 1, j);
@@ -419,7 +465,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
     } else {
       const DT accT = w ? __ldcg(J + e0 * ld + s) : DT(0);
       const DT accS = w ? __ldcg(J + e1 * ld + s) : DT(0);
-      jT = -(accT + ATB + Tdot_t * (DT(A.at(aG, j - 2)) - Cx_b)) * (invV_t * iden);
+      jT = -(accT + ATB + Tdot_t * DT(A.at(aG, j - 2) - Cx_b)) * (invV_t * iden);
       dOm = (accS + ASB) * invV_t;
     }
     DT jS;

@@ -41,6 +41,9 @@ static std::vector<int> net_nu(const pj_mech* m, int i) {
   return nu;
 }
 
+static inline bool is_falloff(int k) { return k == PJ_LINDEMANN || k == PJ_TROE || k == PJ_SRI; }
+static inline bool has_third_body(int k) { return k == PJ_THIRD_BODY || is_falloff(k); }
+
 static std::vector<double> alpha_of(const pj_mech* m, int i) {
   std::vector<double> a(m->ns, 1.0);
   for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++) a[m->eff_sp[e]] = m->eff_val[e];
@@ -64,7 +67,7 @@ static bool rate_dependence(const pj_mech* m, int i, std::vector<char>& dep) {
   for (int a = 0; a < PJ_MAX_SP; a++) member(m->reac_sp[i * PJ_MAX_SP + a]);
   if (m->rev[i])
     for (int a = 0; a < PJ_MAX_SP; a++) member(m->prod_sp[i * PJ_MAX_SP + a]);
-  if (m->kind[i] != PJ_ELEMENTARY) {
+  if (has_third_body(m->kind[i])) {
     std::vector<double> al = alpha_of(m, i);
     const double ref = approx ? 1.0 : al[bath];
     for (int k = 0; k < ns - 1; k++)
@@ -91,7 +94,7 @@ static int validate(const pj_mech* m) {
     return fail(PJ_ERR_MECH, "eff_ptr must have Nr+1 entries starting at 0");
   for (int i = 0; i < nr; i++) {
     std::string tag = "reaction " + std::to_string(i) + ": ";
-    if (m->kind[i] < PJ_ELEMENTARY || m->kind[i] > PJ_SRI) return fail(PJ_ERR_MECH, tag + "bad kind");
+    if (m->kind[i] < PJ_ELEMENTARY || m->kind[i] > PJ_CHEB) return fail(PJ_ERR_MECH, tag + "bad kind");
     int nre = 0, npr = 0;
     for (int a = 0; a < PJ_MAX_SP; a++) {
       for (int side = 0; side < 2; side++) {
@@ -105,9 +108,41 @@ static int validate(const pj_mech* m) {
       }
     }
     if (nre == 0 || npr == 0) return fail(PJ_ERR_MECH, tag + "needs at least one reactant and one product");
-    if (!(m->A[i] > 0) || !std::isfinite(m->A[i])) return fail(PJ_ERR_MECH, tag + "A must be > 0");
-    if (!std::isfinite(m->beta[i]) || !std::isfinite(m->Ea[i])) return fail(PJ_ERR_MECH, tag + "bad beta/Ea");
-    if (m->kind[i] >= PJ_LINDEMANN) {
+    const bool pdep = m->kind[i] == PJ_PLOG || m->kind[i] == PJ_CHEB;
+    if (!pdep && (!(m->A[i] > 0) || !std::isfinite(m->A[i]))) return fail(PJ_ERR_MECH, tag + "A must be > 0");
+    if (m->chem[i] && m->kind[i] < PJ_LINDEMANN) return fail(PJ_ERR_MECH, tag + "only falloff reactions can be chemically activated");
+    if (m->chem[i] && m->kind[i] > PJ_SRI) return fail(PJ_ERR_MECH, tag + "only falloff reactions can be chemically activated");
+    if (m->rev_explicit[i]) {
+      if (!m->rev[i]) return fail(PJ_ERR_MECH, tag + "explicit reverse parameters on an irreversible reaction");
+      if (!(m->rev_A[i] > 0) || !std::isfinite(m->rev_A[i]) || !std::isfinite(m->rev_beta[i]) || !std::isfinite(m->rev_Ea[i]))
+        return fail(PJ_ERR_MECH, tag + "bad explicit reverse parameters");
+    }
+    if (m->plog_ptr[i + 1] < m->plog_ptr[i]) return fail(PJ_ERR_MECH, tag + "plog_ptr not monotone");
+    const int np = m->plog_ptr[i + 1] - m->plog_ptr[i];
+    if ((m->kind[i] == PJ_PLOG) != (np > 0)) return fail(PJ_ERR_MECH, tag + "P-log entries exactly for P-log reactions");
+    for (int e = m->plog_ptr[i]; e < m->plog_ptr[i + 1]; e++) {
+      const double* t = &m->plog[(size_t)e * 4];
+      if (!(t[0] > 0) || !(t[1] > 0) || !std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2]) ||
+          !std::isfinite(t[3]))
+        return fail(PJ_ERR_MECH, tag + "bad P-log entry");
+      if (e > m->plog_ptr[i] && !(t[0] > t[-4])) return fail(PJ_ERR_MECH, tag + "P-log pressures must ascend strictly");
+    }
+    if (m->cheb_ptr[i + 1] < m->cheb_ptr[i]) return fail(PJ_ERR_MECH, tag + "cheb_ptr not monotone");
+    const int ncf = m->cheb_ptr[i + 1] - m->cheb_ptr[i];
+    if (m->kind[i] == PJ_CHEB) {
+      const int nT = m->cheb_nT[i], nP = m->cheb_nP[i];
+      const double* rg = &m->cheb_range[(size_t)i * 4];
+      if (nT < 1 || nT > 16 || nP < 1 || nP > 16 || ncf != nT * nP) return fail(PJ_ERR_MECH, tag + "bad Chebyshev shape");
+      if (!(rg[0] > 0) || !(rg[1] > rg[0]) || !(rg[2] > 0) || !(rg[3] > rg[2]) || !std::isfinite(rg[1]) ||
+          !std::isfinite(rg[3]))
+        return fail(PJ_ERR_MECH, tag + "bad Chebyshev range");
+      for (int e = m->cheb_ptr[i]; e < m->cheb_ptr[i + 1]; e++)
+        if (!std::isfinite(m->cheb_coef[e])) return fail(PJ_ERR_MECH, tag + "non-finite Chebyshev coefficient");
+    } else if (ncf != 0) {
+      return fail(PJ_ERR_MECH, tag + "Chebyshev coefficients on a non-Chebyshev reaction");
+    }
+    if (!pdep && (!std::isfinite(m->beta[i]) || !std::isfinite(m->Ea[i]))) return fail(PJ_ERR_MECH, tag + "bad beta/Ea");
+    if (is_falloff(m->kind[i])) {
       if (!(m->A0[i] > 0) || !std::isfinite(m->A0[i])) return fail(PJ_ERR_MECH, tag + "A0 must be > 0");
       if (!std::isfinite(m->beta0[i]) || !std::isfinite(m->Ea0[i])) return fail(PJ_ERR_MECH, tag + "bad beta0/Ea0");
     }
@@ -181,10 +216,20 @@ int mech_build(pj_mech* m) {
   build_pattern(m);
   const int ns = m->ns, nr = m->nr, N = ns + 1, bath = ns - 1;
 
-  // kernel order: stable sort by kind so that each kind's code runs as a block
+  // kernel order: the plain reactions first, then the special ones
+  // (chemically activated, explicit reverse, P-log, Chebyshev), each part
+  // stable-sorted by kind so that each kind's code runs as a block; the
+  // kernels walk the plain part with a loop compiled without the special
+  // cases
+  auto special = [&](int i) { return m->chem[i] || m->rev_explicit[i] || m->kind[i] >= PJ_PLOG; };
   m->perm.resize(nr);
   for (int i = 0; i < nr; i++) m->perm[i] = i;
-  std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) { return m->kind[a] < m->kind[b]; });
+  std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) {
+    const int sa = special(a) ? 1 : 0, sb = special(b) ? 1 : 0;
+    return sa != sb ? sa < sb : m->kind[a] < m->kind[b];
+  });
+  int nr_plain = 0;
+  while (nr_plain < nr && !special(m->perm[nr_plain])) nr_plain++;
 
   std::vector<double> nasa((size_t)ns * NASA_STRIDE, 0.0), wfac(ns);
   for (int k = 0; k < ns; k++) {
@@ -204,16 +249,51 @@ int mech_build(pj_mech* m) {
   std::vector<double> eff_am1;
   std::vector<RowNu> rows;
   std::vector<char> dep;
+  std::vector<double> tab;  // P-log entries and Chebyshev blocks
+  bool has_pdep = false;
   for (int q = 0; q < nr; q++) {
     const int i = m->perm[q];
     Rxn& r = rx[q];
     std::memset(&r, 0, sizeof(Rxn));
     r.kind = m->kind[i];
-    r.rev = m->rev[i] ? 1 : 0;
-    r.lnA = std::log(m->A[i]);
-    r.beta = m->beta[i];
-    r.theta = m->Ea[i] / R_CAL;
-    if (r.kind >= PJ_LINDEMANN) {
+    r.rev = m->rev[i] ? (m->rev_explicit[i] ? 2 : 1) : 0;
+    const bool pdep = r.kind == PJ_PLOG || r.kind == PJ_CHEB;
+    r.lnA = pdep ? 0.0 : std::log(m->A[i]);
+    r.beta = pdep ? 0.0 : m->beta[i];
+    r.theta = pdep ? 0.0 : m->Ea[i] / R_CAL;
+    r.chem = m->chem[i] ? 1 : 0;
+    r.tab_lo = (int32_t)tab.size();
+    if (r.rev == 2) {
+      tab.push_back(std::log(m->rev_A[i]));
+      tab.push_back(m->rev_beta[i]);
+      tab.push_back(m->rev_Ea[i] / R_CAL);
+    }
+    if (r.kind == PJ_PLOG) {
+      // (ln P, ln A, beta, theta) per entry
+      for (int e = m->plog_ptr[i]; e < m->plog_ptr[i + 1]; e++) {
+        const double* t = &m->plog[(size_t)e * 4];
+        tab.push_back(std::log(t[0]));
+        tab.push_back(std::log(t[1]));
+        tab.push_back(t[2]);
+        tab.push_back(t[3] / R_CAL);
+      }
+      r.tab_n = (int16_t)(m->plog_ptr[i + 1] - m->plog_ptr[i]);
+      has_pdep = true;
+    } else if (r.kind == PJ_CHEB) {
+      // T~ = cT1 / T + cT0, P~ = cP1 ln P + cP0, then ln10 * a_tp (ln k directly)
+      const double* rg = &m->cheb_range[(size_t)i * 4];
+      const double iTmin = 1.0 / rg[0], iTmax = 1.0 / rg[1];
+      const double lPmin = std::log(rg[2]), lPmax = std::log(rg[3]);
+      tab.push_back(2.0 / (iTmax - iTmin));
+      tab.push_back(-(iTmin + iTmax) / (iTmax - iTmin));
+      tab.push_back(2.0 / (lPmax - lPmin));
+      tab.push_back(-(lPmin + lPmax) / (lPmax - lPmin));
+      for (int e = m->cheb_ptr[i]; e < m->cheb_ptr[i + 1]; e++) tab.push_back(LN10 * m->cheb_coef[e]);
+      r.tab_n = (int16_t)m->cheb_nT[i];
+      r.tab_m = (int16_t)m->cheb_nP[i];
+      has_pdep = true;
+    }
+    if (is_falloff(r.kind)) {
       r.lnA0 = std::log(m->A0[i]);
       r.beta0 = m->beta0[i];
       r.theta0 = m->Ea0[i] / R_CAL;
@@ -259,9 +339,9 @@ int mech_build(pj_mech* m) {
     r.dnu = dnu;
     r.dW = dW;
     std::vector<double> al = alpha_of(m, i);
-    r.alpha_bath = r.kind != PJ_ELEMENTARY ? al[bath] : 1.0;
+    r.alpha_bath = has_third_body(r.kind) ? al[bath] : 1.0;
     r.eff_lo = (int32_t)eff_sp.size();
-    if (r.kind != PJ_ELEMENTARY) {
+    if (has_third_body(r.kind)) {
       for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++) {
         if (m->eff_val[e] == 1.0) continue;  // default efficiency: no term
         eff_sp.push_back(m->eff_sp[e]);
@@ -318,7 +398,8 @@ int mech_build(pj_mech* m) {
   const size_t o_pcsc = align256(o_pcsr + (size_t)N * N * sizeof(int32_t));
   const size_t o_perm = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
   const size_t o_etab = align256(o_perm + (size_t)nr * sizeof(int32_t));
-  const size_t total = align256(o_etab + 256 * sizeof(double));
+  const size_t o_tab = align256(o_etab + 256 * sizeof(double));
+  const size_t total = align256(o_tab + tab.size() * sizeof(double));
   // 2^(j/256) in extended precision, rounded once to double
   double etab[256];
   for (int j = 0; j < 256; j++) etab[j] = (double)std::exp2((long double)j / 256.0L);
@@ -335,6 +416,7 @@ int mech_build(pj_mech* m) {
   put(o_pcsc, m->pos_csc.data(), m->pos_csc.size() * sizeof(int32_t));
   put(o_perm, m->perm.data(), m->perm.size() * sizeof(int32_t));
   put(o_etab, etab, sizeof etab);
+  put(o_tab, tab.data(), tab.size() * sizeof(double));
 
   // Without any CUDA device the handle stays host-only: its pattern can be
   // queried, evaluation calls fail with PJ_ERR_CUDA.
@@ -372,6 +454,9 @@ int mech_build(pj_mech* m) {
   dm.pos_csc = reinterpret_cast<const int32_t*>(b + o_pcsc);
   dm.perm = reinterpret_cast<const int32_t*>(b + o_perm);
   dm.exp_tab = reinterpret_cast<const double*>(b + o_etab);
+  dm.tab = reinterpret_cast<const double*>(b + o_tab);
+  dm.has_pdep = has_pdep ? 1 : 0;
+  dm.nr_plain = nr_plain;
   return lu_build(m);
 }
 
@@ -442,6 +527,30 @@ extern "C" int pj_mech_create(const pj_mech_desc* d, pj_mech** out) {
       cp_i(m->eff_sp, d->eff_sp, ne);
       cp_d(m->eff_val, d->eff_val, ne);
     }
+    // less common reaction types: absent arrays mean "none"
+    auto opt_i = [&](std::vector<int32_t>& v, const int32_t* src, size_t len) {
+      if (src) v.assign(src, src + len); else v.assign(len, 0);
+    };
+    auto opt_d = [&](std::vector<double>& v, const double* src, size_t len) {
+      if (src) v.assign(src, src + len); else v.assign(len, 0.0);
+    };
+    opt_i(m->chem, d->chem, nr);
+    opt_i(m->rev_explicit, d->rev_explicit, nr);
+    opt_d(m->rev_A, d->rev_A, nr);
+    opt_d(m->rev_beta, d->rev_beta, nr);
+    opt_d(m->rev_Ea, d->rev_Ea, nr);
+    opt_i(m->plog_ptr, d->plog_ptr, (size_t)nr + 1);
+    opt_i(m->cheb_ptr, d->cheb_ptr, (size_t)nr + 1);
+    opt_i(m->cheb_nT, d->cheb_nT, nr);
+    opt_i(m->cheb_nP, d->cheb_nP, nr);
+    opt_d(m->cheb_range, d->cheb_range, (size_t)nr * 4);
+    const int npl = m->plog_ptr[nr], ncc = m->cheb_ptr[nr];
+    if (npl < 0 || ncc < 0 || (npl > 0 && !d->plog) || (ncc > 0 && !d->cheb_coef)) {
+      delete m;
+      return fail(PJ_ERR_ARG, "pj_mech_create: P-log or Chebyshev counts without data");
+    }
+    opt_d(m->plog, d->plog, (size_t)npl * 4);
+    opt_d(m->cheb_coef, d->cheb_coef, (size_t)ncc);
   } catch (...) {
     delete m;
     return fail(PJ_ERR_NOMEM, "pj_mech_create: out of host memory");
@@ -503,6 +612,18 @@ extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech*
     m->troe_n = src->troe_n;
     m->eff_ptr = src->eff_ptr;
     m->eff_sp = src->eff_sp;
+    m->chem = src->chem;
+    m->rev_explicit = src->rev_explicit;
+    m->rev_A = src->rev_A;
+    m->rev_beta = src->rev_beta;
+    m->rev_Ea = src->rev_Ea;
+    m->plog_ptr = src->plog_ptr;
+    m->plog = src->plog;
+    m->cheb_ptr = src->cheb_ptr;
+    m->cheb_nT = src->cheb_nT;
+    m->cheb_nP = src->cheb_nP;
+    m->cheb_range = src->cheb_range;
+    m->cheb_coef = src->cheb_coef;
   } catch (...) {
     delete m;
     return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
@@ -541,7 +662,9 @@ extern "C" int pj_mech_load(const char* path, pj_mech** out) {
   if (!in) return fail(PJ_ERR_ARG, std::string("pj_mech_load: cannot open ") + path);
   std::string tok;
   auto expect = [&](const char* w) { return (in >> tok) && tok == w; };
-  if (!expect("PJMECH") || !expect("1")) return fail(PJ_ERR_MECH, "pj_mech_load: not a PJMECH 1 file");
+  int version = 0;
+  if (!expect("PJMECH") || !(in >> version) || (version != 1 && version != 2))
+    return fail(PJ_ERR_MECH, "pj_mech_load: not a PJMECH 1 or 2 file");
   int ns = 0, nr = 0;
   if (!expect("SPECIES") || !(in >> ns) || ns < 2 || ns > 1000000) return fail(PJ_ERR_MECH, "pj_mech_load: bad SPECIES record");
   std::vector<double> W(ns), Tm(ns), lo(7 * ns), hi(7 * ns);
@@ -558,6 +681,8 @@ extern "C" int pj_mech_load(const char* path, pj_mech** out) {
   std::vector<int32_t> kind(nr), rev(nr), rsp((size_t)nr * PJ_MAX_SP, -1), rnu((size_t)nr * PJ_MAX_SP, 0),
       psp((size_t)nr * PJ_MAX_SP, -1), pnu((size_t)nr * PJ_MAX_SP, 0), tn(nr), eptr(nr + 1, 0), esp;
   std::vector<double> A(nr), b(nr), Ea(nr), A0(nr), b0(nr), Ea0(nr), troe((size_t)nr * 4), sri((size_t)nr * 5), eval;
+  std::vector<int32_t> chem(nr, 0), revx(nr, 0), pptr(nr + 1, 0), cptr(nr + 1, 0), cnT(nr, 0), cnP(nr, 0);
+  std::vector<double> rA(nr, 0.0), rb(nr, 0.0), rE(nr, 0.0), plog, crange((size_t)nr * 4, 0.0), ccoef;
   for (int i = 0; i < nr; i++) {
     int cnt;
     if (!(in >> kind[i] >> rev[i])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated reaction record");
@@ -582,6 +707,28 @@ extern "C" int pj_mech_load(const char* path, pj_mech** out) {
       eval.push_back(v);
     }
     eptr[i + 1] = (int32_t)esp.size();
+    if (version >= 2) {
+      int np;
+      if (!(in >> chem[i] >> revx[i] >> rA[i] >> rb[i] >> rE[i])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated reverse data");
+      if (!(in >> np) || np < 0 || np > 1000000) return fail(PJ_ERR_MECH, "pj_mech_load: bad P-log count");
+      for (int e = 0; e < 4 * np; e++) {
+        double v;
+        if (!(in >> v)) return fail(PJ_ERR_MECH, "pj_mech_load: truncated P-log data");
+        plog.push_back(v);
+      }
+      if (!(in >> cnT[i] >> cnP[i]) || cnT[i] < 0 || cnP[i] < 0 || cnT[i] > 16 || cnP[i] > 16)
+        return fail(PJ_ERR_MECH, "pj_mech_load: bad Chebyshev shape");
+      if (cnT[i] * cnP[i] > 0) {
+        for (int j = 0; j < 4; j++) if (!(in >> crange[(size_t)i * 4 + j])) return fail(PJ_ERR_MECH, "pj_mech_load: truncated Chebyshev range");
+        for (int e = 0; e < cnT[i] * cnP[i]; e++) {
+          double v;
+          if (!(in >> v)) return fail(PJ_ERR_MECH, "pj_mech_load: truncated Chebyshev coefficients");
+          ccoef.push_back(v);
+        }
+      }
+    }
+    pptr[i + 1] = (int32_t)(plog.size() / 4);
+    cptr[i + 1] = (int32_t)ccoef.size();
   }
   if (!expect("END")) return fail(PJ_ERR_MECH, "pj_mech_load: missing END");
   pj_mech_desc d{};
@@ -593,5 +740,9 @@ extern "C" int pj_mech_load(const char* path, pj_mech** out) {
   d.A = A.data(); d.beta = b.data(); d.Ea = Ea.data(); d.A0 = A0.data(); d.beta0 = b0.data(); d.Ea0 = Ea0.data();
   d.troe = troe.data(); d.troe_n = tn.data(); d.sri = sri.data();
   d.eff_ptr = eptr.data(); d.eff_sp = esp.data(); d.eff_val = eval.data();
+  d.chem = chem.data(); d.rev_explicit = revx.data(); d.rev_A = rA.data(); d.rev_beta = rb.data(); d.rev_Ea = rE.data();
+  d.plog_ptr = pptr.data(); d.plog = plog.data();
+  d.cheb_ptr = cptr.data(); d.cheb_nT = cnT.data(); d.cheb_nP = cnP.data(); d.cheb_range = crange.data();
+  d.cheb_coef = ccoef.data();
   return pj_mech_create(&d, out);
 }

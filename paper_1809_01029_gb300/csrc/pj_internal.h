@@ -37,7 +37,7 @@ enum : int32_t {
 
 // One reaction, packed for warp-uniform loads (every thread of a warp reads
 // the same record).  Reactions are stored in kernel order (see perm).
-struct alignas(16) Rxn {
+struct alignas(8) Rxn {
   double lnA, beta, theta;        // k = exp(lnA + beta lnT - theta/T), theta = Ea/R_cal [K]
   double lnA0, beta0, theta0;     // low-pressure limit (falloff)
   double dnu;                     // sum_k nu_k (equilibrium-constant pressure factor)
@@ -45,7 +45,7 @@ struct alignas(16) Rxn {
   double alpha_bath;              // third-body efficiency of the bath gas
   double fp[5];                   // Troe: a, 1/T3, 1/T1, T2, has_T2 ; SRI: a, b, 1/c, d, e
   double nud[2 * PJ_MAX_SP];      // stoichiometric coefficients as doubles
-  int32_t kind, rev;
+  int32_t kind, rev;              // rev: 0 irreversible, 1 k_r = k_f / K_c, 2 explicit (DevMech::tab)
   int32_t nreac, nprod;
   int32_t shape[2];               // SH_* of the reactant and product sides
   int32_t sp[2 * PJ_MAX_SP];      // reactants [0, nreac), products [PJ_MAX_SP, PJ_MAX_SP + nprod)
@@ -53,7 +53,10 @@ struct alignas(16) Rxn {
   int32_t eff_lo, eff_hi;         // non-default efficiencies in eff_sp / eff_am1
   int32_t row_lo, row_hi;         // species rows (k < Ns-1, net nu != 0) in rows[]
   int32_t dense;                  // rate depends on every species (bath gas involved)
-  int32_t pad;
+  int32_t chem;                   // chemically-activated falloff
+  int32_t tab_lo;                 // DevMech::tab: explicit reverse (ln A, beta, theta) when rev == 2,
+                                  // then the P-log entries / Chebyshev block
+  int16_t tab_n, tab_m;           // P-log entries / Chebyshev N_T, N_P
 };
 
 struct RowNu {
@@ -76,6 +79,11 @@ struct DevMech {
   const int32_t* pos_csc;         // [N*N] full -> CSC value index, -1 if absent
   const int32_t* perm;            // [nr] kernel order -> original reaction index
   const double* exp_tab;          // [256] 2^(j/256), correctly rounded (pj_exp)
+  const double* tab;              // P-log entries (ln P, ln A, beta, theta) and Chebyshev
+                                  // blocks (cT1, cT0, cP1, cP0, ln10 * a_tp row-major)
+  int32_t has_pdep;               // some reaction depends on P (P-log, Chebyshev)
+  int32_t nr_plain;               // plain reactions (kernel order): none chemically activated,
+                                  // with explicit reverse parameters, P-log or Chebyshev
 };
 
 // Index tables of the Newton-matrix LU (lu_symbolic.cpp, lu.cu); pivot
@@ -103,6 +111,9 @@ struct pj_mech {
   // host copies of the description
   std::vector<double> W, T_mid, nasa_low, nasa_high, A, beta, Ea, A0, beta0, Ea0, troe, sri, eff_val;
   std::vector<int32_t> kind, rev, reac_sp, reac_nu, prod_sp, prod_nu, troe_n, eff_ptr, eff_sp;
+  // less common reaction types (empty when absent)
+  std::vector<int32_t> chem, rev_explicit, plog_ptr, cheb_ptr, cheb_nT, cheb_nP;
+  std::vector<double> rev_A, rev_beta, rev_Ea, plog, cheb_range, cheb_coef;
   // derived
   std::vector<int32_t> perm;          // kernel order -> original reaction index
   std::vector<int32_t> csr_ptr, csr_idx, csc_ptr, csc_idx;

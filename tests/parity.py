@@ -87,3 +87,27 @@ def equilibrated_backward_ratio(M, x, b, D, u):
     r = np.abs(np.einsum("ijn,jn->in", At, xt) - bt).max(axis=0)
     den = np.abs(At).sum(axis=1).max(axis=0) * np.abs(xt).max(axis=0) + np.abs(bt).max(axis=0)
     return r / den / (N * u)
+
+
+def lu_solve_ratio(L, U, xp, bp, u):
+    """Residual of the computed solution against the computed factors, in
+    pivot order (xp = x[perm], bp = b[perm]): max |L U x - b| / (N u (|L||U||x|
+    + |b|)).  Triangular substitution is componentwise backward stable, so
+    this is a small constant whatever the growth of the factors."""
+    N = L.shape[0]
+    mv = lambda A, v: np.einsum("ijn,jn->in", A, v)
+    r = np.abs(mv(L, mv(U, xp)) - bp)
+    env = mv(np.abs(L), mv(np.abs(U), np.abs(xp))) + np.abs(bp)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(r == 0, 0.0, r / (N * u * env))
+    return float(q.max())
+
+
+def equilibrated_growth(L, U, A, Dp):
+    """Per state, the growth of LU in the scaled variables (Dp: the states'
+    magnitudes in pivot order): || |L||U| ||_inf / ||A||_inf after scaling rows
+    by 1/Dp and columns by Dp."""
+    mm = lambda a, b: np.moveaxis(np.matmul(np.moveaxis(a, 2, 0), np.moveaxis(b, 2, 0)), 0, 2)
+    sc = Dp[None, :, :] / Dp[:, None, :]
+    E = mm(np.abs(L), np.abs(U)) * sc
+    return E.sum(axis=1).max(axis=0) / (np.abs(A) * sc).sum(axis=1).max(axis=0)

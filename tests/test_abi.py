@@ -139,10 +139,10 @@ def test_no_device_means_no_silent_fallback(lib):
     assert rc == N.PJ_ERR_CUDA
 
 
-@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "h2co13", "gri53", "usc111", "ic5874"])
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53", "usc111", "ic5874"])
 def test_approximate_pattern_bit_exact_against_oracle(lib, mechs, name):
     """The approximate Jacobian form (Sec. 3.4) has its own, sparser pattern."""
-    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency") else mechs(name)
+    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency", "all_types") else mechs(name)
     h = pj.pj_mech_create(m)
     ha = h.with_jacobian_form(pj.PJ_JAC_APPROX)
     assert (h.jacobian_form, ha.jacobian_form) == (pj.PJ_JAC_EXACT, pj.PJ_JAC_APPROX)
@@ -168,7 +168,7 @@ def test_jacobian_form_rejects_unknown_form(lib, mechs):
 def test_lu_ordering_and_pattern_bit_exact_against_oracle(lib, mechs, name, form):
     """The Newton-matrix LU's symbolic phase (pivot order, fill, storage
     order) is index work: identical to the oracle's."""
-    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency") else mechs(name)
+    m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency", "all_types") else mechs(name)
     h = pj.pj_mech_create(m)
     if form:
         h = h.with_jacobian_form(pj.PJ_JAC_APPROX)

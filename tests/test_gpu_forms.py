@@ -26,7 +26,7 @@ def pj():
 
 
 def _mech(mechs, name):
-    if name in ("all_kinds", "bath_efficiency"):
+    if name in ("all_kinds", "bath_efficiency", "all_types"):
         return getattr(tm, name)()
     return mechs(name)
 
@@ -37,7 +37,7 @@ def dev(a):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name,n,gamma", [("all_kinds", 40, 1.0), ("gri53", 48, 0.5), ("usc111", 16, 1.0)])
+@pytest.mark.parametrize("name,n,gamma", [("all_kinds", 40, 1.0), ("all_types", 35, 1.0), ("gri53", 48, 0.5), ("usc111", 16, 1.0)])
 def test_newton_matrix_f32_against_fp64_oracle(pj, mechs, name, n, gamma, mode):
     import torch
     m = _mech(mechs, name)
@@ -49,6 +49,15 @@ def test_newton_matrix_f32_against_fp64_oracle(pj, mechs, name, n, gamma, mode):
     M_ref = -(hs * gamma)[None, None, :] * J
     M_ref[np.arange(N1), np.arange(N1)] += 1.0
     scale = np.abs(M_ref) + (hs * gamma)[None, None, :] * env
+    # the FP32 form's accuracy holds for states whose Newton matrix stays well
+    # inside FP32's range (the tiny all-types mechanism's unphysical
+    # thermochemistry drives some entries past 1e40)
+    keep = ((hs * gamma)[None, None, :] * env).max(axis=(0, 1)) < 1e30
+    assert keep.sum() >= n // 4
+    sel = np.flatnonzero(keep)
+    phi, par, hs, J, env, M_ref, scale = (phi[:, sel], par[sel], hs[sel], J[..., sel], env[..., sel],
+                                          M_ref[..., sel], scale[..., sel])
+    n = len(sel)
     f_ref, f_env = oracle.source_term_envelope(m, mode, phi, par)
     d_phi, d_par, d_h = dev(phi), dev(par), dev(hs)
     dphi = torch.empty((N1, n), dtype=torch.float64, device="cuda")
@@ -80,7 +89,7 @@ def _y_env(m, mode, phi, par):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name,n", [("all_kinds", 45), ("bath_efficiency", 33), ("h2co13", 100), ("gri53", 70)])
+@pytest.mark.parametrize("name,n", [("all_kinds", 45), ("bath_efficiency", 33), ("all_types", 39), ("h2co13", 100), ("gri53", 70)])
 def test_vjp_against_oracle(pj, mechs, name, n, mode):
     m = _mech(mechs, name)
     h = pj.pj_mech_create(m)

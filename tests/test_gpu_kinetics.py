@@ -21,7 +21,7 @@ def pj():
 
 
 def _mech(mechs, name):
-    if name in ("all_kinds", "bath_efficiency"):
+    if name in ("all_kinds", "bath_efficiency", "all_types"):
         return getattr(tm, name)()
     return mechs(name)
 
@@ -36,7 +36,7 @@ def to_dev(a, ld=None):
     return buf[:, : a.shape[1]]
 
 
-SRC_CASES = [("all_kinds", 37), ("bath_efficiency", 33), ("h2co13", 4096), ("gri53", 777), ("usc111", 301)]
+SRC_CASES = [("all_kinds", 37), ("bath_efficiency", 33), ("all_types", 41), ("h2co13", 4096), ("gri53", 777), ("usc111", 301)]
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
@@ -50,7 +50,7 @@ def test_source_terms_match_oracle(pj, mechs, name, n, mode):
     check_close(out, ref, env, RTOL_SRC, ATOL_SRC, f"{name} mode={mode}")
 
 
-JAC_CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("h2co13", 200), ("gri53", 70), ("usc111", 20)]
+JAC_CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("all_types", 36), ("h2co13", 200), ("gri53", 70), ("usc111", 20)]
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])

@@ -14,7 +14,7 @@ U = 2.0 ** -53
 
 
 def _mech(name):
-    return getattr(tm, name)() if name in ("all_kinds", "bath_efficiency") else synth.make_mechanism(name)
+    return getattr(tm, name)() if name in ("all_kinds", "bath_efficiency", "all_types") else synth.make_mechanism(name)
 
 
 def fd_tolerance(m, mode, phi, par):
@@ -25,7 +25,7 @@ def fd_tolerance(m, mode, phi, par):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "h2co13", "gri53"])
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53"])
 def test_fd_jacobian_within_truncation_and_rounding(name, mode):
     m = _mech(name)
     phi, par = synth.make_states(m, 12, 31, mode)

@@ -322,7 +322,7 @@ def test_jacobian_closed_form_first_order():
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
 @pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "h2co13", "gri53"])
 def test_jacobian_matches_central_differences(mechs, mk, mode):
-    m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency") else mechs(mk)
+    m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency", "all_types") else mechs(mk)
     # no vanishing mole fractions, so a relative step of 1e-6 balances the
     # O(h^2) truncation against the O(u/h) rounding of the difference
     phi, par = synth.make_states(m, 6, 17, mode, alpha=5.0)
@@ -344,7 +344,7 @@ def test_jacobian_matches_central_differences(mechs, mk, mode):
 
 @pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "h2co13", "gri53"])
 def test_pattern_superset_and_tight(mechs, mk):
-    m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency") else mechs(mk)
+    m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency", "all_types") else mechs(mk)
     mask = K.sparsity_pattern(m)
     phi, par = synth.make_states(m, 24, 23, synth.CONP)
     J = K.jacobian(m, synth.CONP, phi, par)

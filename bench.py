@@ -22,7 +22,11 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# the CPU oracle is timed on one core: keep numpy's BLAS single-threaded
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -37,6 +41,9 @@ W_EXP, W_LOG, W_DIV = 16.0, 30.2, 5.7
 # FP64 peak derived from unit counts and clock: 2 DFMA / clock / SM
 # (1.25 TFLOP/s nominal for GB300) x 152 SMs x 2070 MHz.
 FP64_DFMA_PER_CLK_SM = 2.0
+
+
+CPU_SAMPLE = 4096   # states of the oracle's timed sample (10-30 s of one core)
 
 
 def fp64_work_per_state(m, jacobian=True):
@@ -56,7 +63,14 @@ def fp64_work_per_state(m, jacobian=True):
         sre, spr = sum(v for _, v in r), sum(v for _, v in p)
         kind = int(m.kind[i])
         w += 2 + W_EXP + (sre - 1) + 1                  # kf and forward product
-        if m.reversible[i]:
+        if kind == synth.PLOG:                          # segment search, two ln k, interpolation
+            w += int(m.plog_ptr[i + 1] - m.plog_ptr[i]) + 2 * 2 + 3
+        elif kind == synth.CHEB:                        # reduced T and P, recurrences, double sum
+            nT, nP = (int(x) for x in m.cheb_shape[i])
+            w += 4 + 2 * (nT + nP) + nT * nP + nT
+        if m.reversible[i] and m.rev_explicit[i]:
+            w += 2 + W_EXP + (spr - 1) + 1              # explicit reverse Arrhenius
+        elif m.reversible[i]:
             w += (nre + npr) + 2 + W_EXP + (spr - 1) + 1
         if kind != synth.ELEMENTARY:
             w += len(m.efficiencies(i))
@@ -71,9 +85,14 @@ def fp64_work_per_state(m, jacobian=True):
             w += 2 + nre + (nre + npr)                  # dln kf/dT, dRf/dC, sum nu h
             if m.reversible[i]:
                 w += 3 + npr
+            if kind == synth.PLOG:
+                w += 6
+            elif kind == synth.CHEB:
+                nT, nP = (int(x) for x in m.cheb_shape[i])
+                w += 2 * (nT + nP) + nT * nP + nT + 2
             if kind == synth.THIRD_BODY:
                 w += 4
-            elif kind != synth.ELEMENTARY:
+            elif kind in (synth.LINDEMANN, synth.TROE, synth.SRI):
                 w += 2 + 12 + W_DIV
                 if kind == synth.TROE:
                     w += 16 + W_DIV
@@ -81,7 +100,7 @@ def fp64_work_per_state(m, jacobian=True):
                     w += 10 + W_DIV
             w += 4 + (nre + npr) + 4 + 3 + 4          # dR/dT, dR/dS, dq/dT, dq/dS, dE, accumulators
             rows = sum(1 for k in range(ns - 1) if (sum(v for kk, v in p if kk == k) - sum(v for kk, v in r if kk == k)) != 0)
-            slots = nre + (npr if m.reversible[i] else 0) + (len(m.efficiencies(i)) if kind else 0)
+            slots = nre + (npr if m.reversible[i] else 0) + (len(m.efficiencies(i)) if kind != synth.ELEMENTARY else 0)
             w += 2 * rows + slots * (1 + rows + 2)     # products feeding the L2 reductions
     w += ns + 2 * (ns - 1) + W_DIV + 10                 # energy and state equations
     if jacobian:
@@ -315,8 +334,42 @@ def other_workloads(pj, synth, torch, dev, stream):
     out["gri53_64k_analytical_over_fd"] = tf / ta
     del J, f, w, phi, par
     torch.cuda.empty_cache()
+    out.update(types_workload(pj, synth, torch, dev, stream))
     out.update(lu_workloads(pj, synth, torch, dev, stream))
     out.update(ragged_workload(pj, synth, torch, dev, stream))
+    return out
+
+
+def types_workload(pj, synth, torch, dev, stream):
+    """The 53/325 mechanism with every less common reaction type (P-log,
+    Chebyshev, chemically activated, explicit reverse), 1,048,576 states:
+    source terms + CSR Jacobian, and its FP64-pipe fraction."""
+    m = synth.make_mechanism("gri53_types")
+    h = pj.pj_mech_create(m)
+    n = 1048576
+    phi_h, par_h = synth.make_states(m, n, 2018 + 2, synth.CONP)
+    phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+    del phi_h, par_h
+    f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device=dev)
+    wb = h.workspace_size(pj.PJ_OP_JACOBIAN, n)
+    w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    J = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    t = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f,
+                                                                status, w, wb, stream), reps=3)
+    ws = h.workspace_size(pj.PJ_OP_SOURCE, n)
+    w2 = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+    ts = _time(torch, stream, lambda: pj.pj_eval_source_terms(h, synth.CONP, n, par, phi, n, f, status, w2, ws,
+                                                              stream), reps=5)
+    assert int(status.item()) == 0
+    props = torch.cuda.get_device_properties(dev)
+    peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * 2070.0e6
+    out = {"gri53types_1m_jacobian_csr": n / (t * 1e-3),
+           "gri53types_1m_jacobian_csr_fp64_frac": fp64_work_per_state(m) * n / (t * 1e-3) / peak,
+           "gri53types_1m_source": n / (ts * 1e-3),
+           "gri53types_1m_source_fp64_frac": fp64_work_per_state(m, jacobian=False) * n / (ts * 1e-3) / peak}
+    del J, f, w, w2, phi, par
+    torch.cuda.empty_cache()
     return out
 
 
@@ -545,13 +598,18 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             return a.elapsed_time(b) / reps
-        for md, nm in ((synth.CONP, "conp"), (synth.CONV, "conv")):
-            t_src = timeit(lambda: pj.pj_eval_source_terms(h, md, n, par, phi, n, dphi, status, work_s, wbs, stream))
+        # constant-volume cases on constant-volume states of the same recipe
+        phv_h, pav_h = synth.make_states(m, n, 2018 + 2 + 1000 * rank, synth.CONV)
+        phv, pav = torch.from_numpy(phv_h).to(dev), torch.from_numpy(pav_h).to(dev)
+        del phv_h, pav_h
+        for md, nm, ph_, pa_ in ((synth.CONP, "conp", phi, par), (synth.CONV, "conv", phv, pav)):
+            t_src = timeit(lambda: pj.pj_eval_source_terms(h, md, n, pa_, ph_, n, dphi, status, work_s, wbs, stream))
             variants[f"source_{nm}"] = n / (t_src * 1e-3)
         variants["jacobian_csc_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
             h, mode, pj.PJ_CSC, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
         variants["jacobian_csr_conv"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
-            h, synth.CONV, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
+            h, synth.CONV, pj.PJ_CSR, n, pav, phv, n, vals, dphi, status, work, wb, stream)) * 1e-3)
+        del phv, pav
         ha = h.with_jacobian_form(pj.PJ_JAC_APPROX)
         wba = ha.workspace_size(pj.PJ_OP_JACOBIAN, n)
         worka = torch.empty(max(wba, 1), dtype=torch.uint8, device=dev)
@@ -612,9 +670,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = oracle_baseline(m, mode, 48, 2018 + 2)
+        v, dt = oracle_baseline(m, mode, CPU_SAMPLE, 2018 + 2)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"48 states of the {WORKLOAD} workload: numpy source terms + complex-step CSR Jacobian "
+               "sample": f"{CPU_SAMPLE} states of the {WORKLOAD} workload: numpy source terms + complex-step CSR Jacobian "
                          f"({dt:.1f} s)"}
 
     if rank == 0:

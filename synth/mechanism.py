@@ -153,6 +153,14 @@ class MechSpec:
     f_sri: float
     seed: int
     f_reversible: float = 0.9
+    # less common reaction types, converted from the plain mechanism of the
+    # same seed: P-log and Chebyshev replace elementary reactions,
+    # chemically-activated falloff a fraction of the falloff reactions,
+    # explicit reverse Arrhenius parameters a fraction of the reversible ones
+    f_plog: float = 0.0
+    f_cheb: float = 0.0
+    f_chem: float = 0.0
+    f_rev_explicit: float = 0.0
 
 
 SPECS = {
@@ -160,6 +168,12 @@ SPECS = {
     "gri53": MechSpec("gri53", 53, 325, 0.10, 0.08, 0.02, 0.01, seed=1809 + 2),
     "usc111": MechSpec("usc111", 111, 784, 0.10, 0.08, 0.02, 0.01, seed=1809 + 3),
     "ic5874": MechSpec("ic5874", 874, 3796, 0.12, 0.10, 0.02, 0.01, seed=1809 + 5),
+    # the 53/325 mechanism with every less common type (none of the paper's
+    # workloads has them): 5 % P-log, 3 % Chebyshev, a third of the falloff
+    # reactions chemically activated, 10 % of the reversible reactions with
+    # explicit reverse parameters
+    "gri53_types": MechSpec("gri53_types", 53, 325, 0.10, 0.08, 0.02, 0.01, seed=1809 + 2,
+                            f_plog=0.05, f_cheb=0.03, f_chem=1.0 / 3.0, f_rev_explicit=0.10),
 }
 
 
@@ -393,7 +407,7 @@ def make_mechanism(spec: MechSpec | str) -> Mechanism:
                 eff_val.append(rng.uniform(0.0, 5.0))
         eff_ptr.append(len(eff_sp))
 
-    return Mechanism(
+    m = Mechanism(
         name=spec.name, species=names, composition=comp, W=W,
         T_mid=np.full(ns, 1000.0), nasa_low=low, nasa_high=high,
         kind=kind, reversible=reversible,
@@ -402,6 +416,71 @@ def make_mechanism(spec: MechSpec | str) -> Mechanism:
         troe=troe, troe_n=troe_n, sri=sri,
         eff_ptr=np.array(eff_ptr, dtype=np.int64), eff_sp=np.array(eff_sp, dtype=np.int64),
         eff_val=np.array(eff_val, dtype=float))
+    if spec.f_plog or spec.f_cheb or spec.f_chem or spec.f_rev_explicit:
+        _add_special_types(m, spec)
+    return m
+
+
+P_ATM = 101325.0
+
+
+def _add_special_types(m: Mechanism, spec: MechSpec) -> None:
+    """Convert reactions of a plain mechanism to the less common types (a
+    separate random stream, so the plain reactions stay those of the plain
+    recipe with the same seed).
+
+    * P-log: 2-5 pressures log-spaced over [0.01, 100] atm; entry m has
+      ln A_m = ln A + U[-2, 2] + g (m - centre) with g ~ U[-0.5, 0.5], beta_m
+      = beta + U[-0.3, 0.3], Ea_m = Ea U[0.9, 1.1].
+    * Chebyshev: N_T x N_P in {4..7} x {2..4}, T in [300, 3000] K, P in
+      [0.01, 100] atm; a_00 ~ U[8, 12] (log10 k), a_10 ~ U[-1.5, -0.2], the
+      other coefficients N(0, 0.3 / (1 + t + p)^2).
+    * chemically activated: the falloff parameters unchanged, the rate
+      becomes k0 F / (1 + Pr).
+    * explicit reverse: ln A_r = ln A + U[-3, 3], beta_r = beta + U[-0.5, 0.5],
+      Ea_r = Ea + U[0, 30000] cal/mol.
+    """
+    rng = np.random.Generator(np.random.PCG64(spec.seed + 7000))
+    nr = m.n_reactions
+    elem = [i for i in range(nr) if m.kind[i] == ELEMENTARY]
+    n_plog = int(round(spec.f_plog * nr))
+    n_cheb = int(round(spec.f_cheb * nr))
+    pick = rng.permutation(elem)[:n_plog + n_cheb]
+    plog_set = set(int(i) for i in pick[:n_plog])
+    cheb_set = set(int(i) for i in pick[n_plog:])
+    plog, cheb = [], []
+    for i in range(nr):
+        if i in plog_set:
+            m.kind[i] = PLOG
+            npts = int(rng.integers(2, 6))
+            Ps = P_ATM * np.logspace(-2.0, 2.0, npts)
+            g = rng.uniform(-0.5, 0.5)
+            lnA = np.log(m.A[i])
+            for j, P in enumerate(Ps):
+                plog.append([P, np.exp(lnA + rng.uniform(-2.0, 2.0) + g * (j - (npts - 1) / 2)),
+                             m.beta[i] + rng.uniform(-0.3, 0.3), m.Ea[i] * rng.uniform(0.9, 1.1)])
+        m.plog_ptr[i + 1] = len(plog)
+        if i in cheb_set:
+            m.kind[i] = CHEB
+            nT, nP = int(rng.integers(4, 8)), int(rng.integers(2, 5))
+            t, q = np.meshgrid(np.arange(nT), np.arange(nP), indexing="ij")
+            a = rng.standard_normal((nT, nP)) * 0.3 / (1.0 + t + q) ** 2
+            a[0, 0] = rng.uniform(8.0, 12.0)
+            a[1, 0] = rng.uniform(-1.5, -0.2)
+            m.cheb_shape[i] = (nT, nP)
+            m.cheb_range[i] = (300.0, 3000.0, 0.01 * P_ATM, 100.0 * P_ATM)
+            cheb += list(a.ravel())
+        m.cheb_ptr[i + 1] = len(cheb)
+    m.plog = np.array(plog, dtype=float).reshape(-1, 4)
+    m.cheb_coef = np.array(cheb, dtype=float)
+    fall = [i for i in range(nr) if m.kind[i] in (LINDEMANN, TROE, SRI)]
+    for i in rng.permutation(fall)[:int(round(spec.f_chem * len(fall)))]:
+        m.chem[i] = True
+    rev = [i for i in range(nr) if m.reversible[i]]
+    for i in rng.permutation(rev)[:int(round(spec.f_rev_explicit * len(rev)))]:
+        m.rev_explicit[i] = True
+        m.rev_arr[i] = (m.A[i] * np.exp(rng.uniform(-3.0, 3.0)), m.beta[i] + rng.uniform(-0.5, 0.5),
+                        m.Ea[i] + rng.uniform(0.0, 30000.0))
 
 
 # --------------------------------------------------------------------------

@@ -111,3 +111,20 @@ def equilibrated_growth(L, U, A, Dp):
     sc = Dp[None, :, :] / Dp[:, None, :]
     E = mm(np.abs(L), np.abs(U)) * sc
     return E.sum(axis=1).max(axis=0) / (np.abs(A) * sc).sum(axis=1).max(axis=0)
+
+
+def y_envelope(m, mode, phi, par):
+    """Absolute rounding envelope of y = (wdot, dT/dt): per species the sum of
+    |nu| (|q'| + |q''|) over the reactions that change it, and the source-term
+    envelope of dT/dt."""
+    import oracle
+    r = oracle.rates(m, mode, phi, par)
+    _, fenv = oracle.source_term_envelope(m, mode, phi, par)
+    nu = r["nu"]
+    ew = np.zeros_like(r["wdot"])
+    for i in range(m.n_reactions):
+        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
+        for k in range(m.n_species):
+            if nu[k, i]:
+                ew[k] += abs(nu[k, i]) * t
+    return np.concatenate([ew, fenv[:1]], axis=0)

@@ -49,7 +49,7 @@ def test_version(lib):
     assert b"pyjac_gb" in lib.pj_version()
 
 
-@pytest.mark.parametrize("name", ["h2co13", "gri53", "usc111"])
+@pytest.mark.parametrize("name", ["h2co13", "gri53", "gri53_types", "usc111"])
 def test_pattern_bit_exact_against_oracle(lib, mechs, name):
     m = mechs(name)
     h = pj.pj_mech_create(m)
@@ -68,12 +68,15 @@ def test_pattern_tiny_mechanisms(lib, mk):
     assert np.array_equal(ptr, rp) and np.array_equal(idx, ci)
 
 
-def test_mechanism_file_round_trip(lib, mechs, tmp_path):
-    m = mechs("gri53")
-    path = str(tmp_path / "gri53.pjmech")
+@pytest.mark.parametrize("name", ["gri53", "gri53_types"])
+def test_mechanism_file_round_trip(lib, mechs, tmp_path, name):
+    m = mechs(name)
+    path = str(tmp_path / f"{name}.pjmech")
     synth.write_mechanism(m, path)
     back = synth.read_mechanism(path)
-    for f in ("W", "nasa_low", "nasa_high", "A", "beta", "Ea", "A0", "troe", "sri", "eff_val"):
+    for f in ("W", "nasa_low", "nasa_high", "kind", "reversible", "A", "beta", "Ea", "A0", "troe", "sri",
+              "eff_val", "chem", "rev_explicit", "rev_arr", "plog_ptr", "plog", "cheb_ptr", "cheb_shape",
+              "cheb_range", "cheb_coef"):
         assert np.array_equal(getattr(m, f), getattr(back, f)), f
     h1 = pj.pj_mech_create(m)
     h2 = pj.pj_mech_load(path)
@@ -139,7 +142,8 @@ def test_no_device_means_no_silent_fallback(lib):
     assert rc == N.PJ_ERR_CUDA
 
 
-@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53", "usc111", "ic5874"])
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53", "gri53_types", "usc111",
+                                  "ic5874"])
 def test_approximate_pattern_bit_exact_against_oracle(lib, mechs, name):
     """The approximate Jacobian form (Sec. 3.4) has its own, sparser pattern."""
     m = getattr(tm, name)() if name in ("all_kinds", "bath_efficiency", "all_types") else mechs(name)
@@ -164,7 +168,8 @@ def test_jacobian_form_rejects_unknown_form(lib, mechs):
 
 
 @pytest.mark.parametrize("form", [0, 1])
-@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "h2co13", "gri53", "usc111"])
+@pytest.mark.parametrize("name", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53", "gri53_types",
+                                  "usc111"])
 def test_lu_ordering_and_pattern_bit_exact_against_oracle(lib, mechs, name, form):
     """The Newton-matrix LU's symbolic phase (pivot order, fill, storage
     order) is index work: identical to the oracle's."""

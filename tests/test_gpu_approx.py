@@ -31,7 +31,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("all_types", 31), ("h2co13", 100), ("gri53", 64), ("usc111", 16)]
+CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("all_types", 31), ("h2co13", 100), ("gri53", 64), ("gri53_types", 40), ("usc111", 16)]
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])

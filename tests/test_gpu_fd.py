@@ -41,7 +41,7 @@ def _mech(mechs, name):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name,n", [("all_kinds", 37), ("bath_efficiency", 20), ("all_types", 25), ("h2co13", 130), ("gri53", 33)])
+@pytest.mark.parametrize("name,n", [("all_kinds", 37), ("bath_efficiency", 20), ("all_types", 25), ("h2co13", 130), ("gri53", 33), ("gri53_types", 21)])
 def test_fd_jacobian_matches_oracle(pj, mechs, name, n, mode):
     import torch
     m = _mech(mechs, name)

@@ -6,7 +6,7 @@ import pytest
 import oracle
 import synth
 from tests import tiny_mechs as tm
-from tests.parity import RTOL_SRC, ATOL_SRC, check_close
+from tests.parity import RTOL_SRC, ATOL_SRC, check_close, y_envelope
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,8 @@ def dev(a):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name,n,gamma", [("all_kinds", 40, 1.0), ("all_types", 35, 1.0), ("gri53", 48, 0.5), ("usc111", 16, 1.0)])
+@pytest.mark.parametrize("name,n,gamma", [("all_kinds", 40, 1.0), ("all_types", 35, 1.0), ("gri53", 48, 0.5),
+                                           ("gri53_types", 40, 1.0), ("usc111", 16, 1.0)])
 def test_newton_matrix_f32_against_fp64_oracle(pj, mechs, name, n, gamma, mode):
     import torch
     m = _mech(mechs, name)
@@ -75,21 +76,9 @@ def test_newton_matrix_f32_against_fp64_oracle(pj, mechs, name, n, gamma, mode):
         assert np.all(e <= NEWTON_ENTRY * conv(m, scale)), (fmt, float(np.max(e / conv(m, scale))))
 
 
-def _y_env(m, mode, phi, par):
-    r = oracle.rates(m, mode, phi, par)
-    _, fenv = oracle.source_term_envelope(m, mode, phi, par)
-    nu = r["nu"]
-    ew = np.zeros_like(r["wdot"])
-    for i in range(m.n_reactions):
-        t = np.abs(r["qf"][i]) + np.abs(r["qr"][i])
-        for k in range(m.n_species):
-            if nu[k, i]:
-                ew[k] += abs(nu[k, i]) * t
-    return np.concatenate([ew, fenv[:1]], axis=0)
-
-
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name,n", [("all_kinds", 45), ("bath_efficiency", 33), ("all_types", 39), ("h2co13", 100), ("gri53", 70)])
+@pytest.mark.parametrize("name,n", [("all_kinds", 45), ("bath_efficiency", 33), ("all_types", 39), ("h2co13", 100), ("gri53", 70),
+                                     ("gri53_types", 50)])
 def test_vjp_against_oracle(pj, mechs, name, n, mode):
     m = _mech(mechs, name)
     h = pj.pj_mech_create(m)
@@ -97,13 +86,13 @@ def test_vjp_against_oracle(pj, mechs, name, n, mode):
     uw, uT = synth.make_cotangents(m.n_species, n, 700 + n)
     y, g_phi, g_th = pj.vjp(h, mode, dev(phi), dev(par), dev(uw), dev(uT))
     y_ref = oracle.outputs_y(m, mode, phi, par)
-    check_close(y.cpu().numpy(), y_ref, _y_env(m, mode, phi, par), RTOL_SRC, ATOL_SRC, f"{name} y")
+    check_close(y.cpu().numpy(), y_ref, y_envelope(m, mode, phi, par), RTOL_SRC, ATOL_SRC, f"{name} y")
     g_ref, th_ref = oracle.vjp(m, mode, phi, par, uw, uT)
     e_phi, e_th = oracle.vjp_envelope(m, mode, phi, par, uw, uT)
     check_close(g_phi.cpu().numpy(), g_ref, e_phi, RTOL_VJP, 1e-300, f"{name} g_phi")
     check_close(g_th.cpu().numpy(), th_ref, e_th, RTOL_VJP, 1e-300, f"{name} g_theta")
     y2 = pj.eval_y(h, mode, dev(phi), dev(par)).cpu().numpy()
-    check_close(y2, y_ref, _y_env(m, mode, phi, par), RTOL_SRC, ATOL_SRC, f"{name} eval_y")
+    check_close(y2, y_ref, y_envelope(m, mode, phi, par), RTOL_SRC, ATOL_SRC, f"{name} eval_y")
 
 
 def test_vjp_deterministic_and_ragged(pj, mechs):
@@ -154,7 +143,7 @@ def test_autograd_function_matches_finite_differences(pj, mechs):
             p1[j, s] += hh
             p2[j, s] -= hh
             fd = (uy(p1) - uy(p2)) / (2 * hh)
-            tol = 1e-4 * e_phi[j, s] + 1e-10 * np.sum(np.abs(u) * _y_env(m, synth.CONP, phi, par)) / hh
+            tol = 1e-4 * e_phi[j, s] + 1e-10 * np.sum(np.abs(u) * y_envelope(m, synth.CONP, phi, par)) / hh
             assert abs(fd - g_phi[j, s]) <= tol, (j, s, fd, g_phi[j, s])
     # parameters: perturb one reaction's ln A / beta / Ea in a new mechanism
     for i in (0, 7, int(np.flatnonzero(m.kind == synth.TROE)[0])):
@@ -174,5 +163,5 @@ def test_autograd_function_matches_finite_differences(pj, mechs):
                 hm = pj.pj_mech_create(mm)
                 vals.append(float((pj.eval_y(hm, synth.CONP, dev(phi), d_par).cpu().numpy() * u).sum()))
             fd = (vals[0] - vals[1]) / (2 * step)
-            tol = 1e-4 * e_th[i, p] + 1e-10 * np.sum(np.abs(u) * _y_env(m, synth.CONP, phi, par)) / step
+            tol = 1e-4 * e_th[i, p] + 1e-10 * np.sum(np.abs(u) * y_envelope(m, synth.CONP, phi, par)) / step
             assert abs(fd - g_th[i, p]) <= tol, (i, p, fd, g_th[i, p])

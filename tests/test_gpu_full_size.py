@@ -1,0 +1,272 @@
+"""Parity at the measured workloads' full sizes, through the same entry points,
+sizes, leading dimensions and workspaces as the benchmark's timed calls (so
+in the launch configuration it times): the outputs of sampled states against
+the oracle, which computes them one state at a time, and properties that hold
+at any size (zero cotangents give exact zeros, no invalid state counted).
+
+Samples cover the first and last thread of the first tiles, a state in the
+middle and the last tiles, and random states."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope
+
+pytestmark = pytest.mark.gpu
+
+NEWTON_ENTRY = 1e-5     # the FP32 Newton matrix's stated per-entry accuracy
+RTOL_VJP = 1e-8
+
+
+@pytest.fixture(scope="module")
+def pj():
+    import paper_1809_01029_gb300 as pj
+    from paper_1809_01029_gb300 import build
+    build.build()
+    pj.load_library()
+    return pj
+
+
+def sample_states(n, k, seed):
+    fixed = [0, 1, 31, 32, 127, 128, n // 2 + 5, n - 129, n - 33, n - 1]
+    rnd = np.random.default_rng(seed).choice(n, size=k, replace=False)
+    return np.unique(np.concatenate([[i for i in fixed if 0 <= i < n], rnd]))
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _cols(torch, t, idx):
+    return t[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+
+
+def _work(torch, h, op, n):
+    wb = h.workspace_size(op, n)
+    return torch.empty(max(wb, 1), dtype=torch.uint8, device="cuda"), wb
+
+
+@pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
+def test_gri53_one_mebi_states_source_and_jacobians(pj, mechs, mode):
+    """53 species / 325 reactions, 1,048,576 states: source terms, CSR, CSC
+    and dense Jacobian of the benchmark's states."""
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m)
+    n = 1 << 20
+    N1 = m.n_species + 1
+    phi_h, par_h = synth.make_states(m, n, 2018 + 2, mode)
+    phi, par = _dev(torch, phi_h), _dev(torch, par_h)
+    idx = sample_states(n, 22, 5 + mode)
+    ps, qs = phi_h[:, idx], par_h[idx]
+    f_ref, f_env = oracle.source_term_envelope(m, mode, ps, qs)
+    J, env = oracle.jacobian_envelope(m, mode, ps, qs)
+    stream = torch.cuda.current_stream()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dphi = torch.empty((N1, n), dtype=torch.float64, device="cuda")
+
+    w, wb = _work(torch, h, pj.PJ_OP_SOURCE, n)
+    pj.pj_eval_source_terms(h, mode, n, par, phi, n, dphi, status, w, wb, stream)
+    check_close(_cols(torch, dphi, idx), f_ref, f_env, RTOL_SRC, ATOL_SRC, "source terms, 1 Mi states")
+    del w
+
+    w, wb = _work(torch, h, pj.PJ_OP_JACOBIAN, n)
+    vals = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
+    for fmt, conv in ((pj.PJ_CSR, oracle.dense_to_csr_values), (pj.PJ_CSC, oracle.dense_to_csc_values)):
+        dphi.fill_(float("nan"))
+        pj.pj_eval_jacobian_sparse(h, mode, fmt, n, par, phi, n, vals, dphi, status, w, wb, stream)
+        check_close(_cols(torch, vals, idx), conv(m, J), conv(m, env), RTOL_JAC, ATOL_JAC, f"fmt={fmt}, 1 Mi states")
+        check_close(_cols(torch, dphi, idx), f_ref, f_env, RTOL_SRC, ATOL_SRC, "f of the Jacobian kernel")
+    del vals
+    torch.cuda.empty_cache()
+    jd = torch.empty((N1 * N1, n), dtype=torch.float64, device="cuda")
+    pj.pj_eval_jacobian_dense(h, mode, n, par, phi, n, jd, dphi, status, w, wb, stream)
+    check_close(_cols(torch, jd, idx).reshape(N1, N1, -1), J, env, RTOL_JAC, ATOL_JAC, "dense, 1 Mi states")
+    assert int(status.item()) == 0
+    del jd, w, dphi
+    torch.cuda.empty_cache()
+
+
+def test_gri53_one_mebi_states_approximate_form(pj, mechs):
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m).with_jacobian_form(pj.PJ_JAC_APPROX)
+    n = 1 << 20
+    phi_h, par_h = synth.make_states(m, n, 2018 + 2, synth.CONP)
+    phi, par = _dev(torch, phi_h), _dev(torch, par_h)
+    idx = sample_states(n, 6, 41)
+    Ja = oracle.jacobian(m, synth.CONP, phi_h[:, idx], par_h[idx], form=oracle.APPROX)
+    _, env = oracle.jacobian_envelope(m, synth.CONP, phi_h[:, idx], par_h[idx])
+    w, wb = _work(torch, h, pj.PJ_OP_JACOBIAN, n)
+    vals = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
+    dphi = torch.empty((m.n_species + 1, n), dtype=torch.float64, device="cuda")
+    pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, vals, dphi, None, w, wb,
+                               torch.cuda.current_stream())
+    conv = lambda a: oracle.dense_to_csr_values(m, a, oracle.APPROX)
+    check_close(_cols(torch, vals, idx), conv(Ja), conv(env), RTOL_JAC, ATOL_JAC, "approximate form, 1 Mi states")
+    del vals, w, dphi
+    torch.cuda.empty_cache()
+
+
+def test_h2co13_all_4096_states(pj, mechs):
+    """13 species / 27 reactions, 4096 states: every state, source terms and
+    CSR Jacobian."""
+    import torch
+    m = mechs("h2co13")
+    h = pj.pj_mech_create(m)
+    n = 4096
+    phi_h, par_h = synth.make_states(m, n, 2018 + 1, synth.CONP)
+    phi, par = _dev(torch, phi_h), _dev(torch, par_h)
+    v = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
+    f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device="cuda")
+    pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, v, f, None, None, 0,
+                               torch.cuda.current_stream())
+    J, env = oracle.jacobian_envelope(m, synth.CONP, phi_h, par_h)
+    f_ref, f_env = oracle.source_term_envelope(m, synth.CONP, phi_h, par_h)
+    check_close(v.cpu().numpy(), oracle.dense_to_csr_values(m, J), oracle.dense_to_csr_values(m, env),
+                RTOL_JAC, ATOL_JAC, "h2co13 4096")
+    check_close(f.cpu().numpy(), f_ref, f_env, RTOL_SRC, ATOL_SRC, "h2co13 4096 source terms")
+
+
+def test_usc111_quarter_mebi_states_newton_and_jacobian(pj, mechs):
+    """111 species / 784 reactions, 262,144 states: the FP32 Newton matrix
+    against the FP64 oracle at its stated accuracy, and the FP64 Jacobian."""
+    import torch
+    m = mechs("usc111")
+    h = pj.pj_mech_create(m)
+    n = 262144
+    N1 = m.n_species + 1
+    phi_h, par_h = synth.make_states(m, n, 2018 + 3, synth.CONP)
+    hs_h = synth.make_step_sizes(n, 2018 + 3)
+    phi, par, hs = _dev(torch, phi_h), _dev(torch, par_h), _dev(torch, hs_h)
+    idx = sample_states(n, 6, 3)
+    J, env = oracle.jacobian_envelope(m, synth.CONP, phi_h[:, idx], par_h[idx])
+    hsel = hs_h[idx]
+    M_ref = -hsel[None, None, :] * J
+    M_ref[np.arange(N1), np.arange(N1)] += 1.0
+    scale = np.abs(M_ref) + hsel[None, None, :] * env
+    # the FP32 form's accuracy is stated for Newton matrices well inside
+    # FP32's range
+    keep = (hsel[None, None, :] * env).max(axis=(0, 1)) < 1e30
+    assert keep.sum() >= len(idx) // 2
+    stream = torch.cuda.current_stream()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    f = torch.empty((N1, n), dtype=torch.float64, device="cuda")
+    w, wb = _work(torch, h, pj.PJ_OP_NEWTON, n)
+    M = torch.empty((h.nnz, n), dtype=torch.float32, device="cuda")
+    pj.pj_newton_matrix_f32(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, hs, 1.0, M, f, status, w, wb, stream)
+    got = _cols(torch, M, idx[keep]).astype(np.float64)
+    conv = lambda a: oracle.dense_to_csr_values(m, a)
+    err = np.abs(got - conv(M_ref[..., keep]))
+    tol = NEWTON_ENTRY * conv(scale[..., keep])
+    assert np.all(err <= tol), float(np.max(err / tol))
+    del M
+    Jd = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
+    pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, Jd, f, status, w, wb, stream)
+    check_close(_cols(torch, Jd, idx), conv(J), conv(env), RTOL_JAC, ATOL_JAC, "usc111 FP64, 256 ki states")
+    assert int(status.item()) == 0
+    del Jd, w, f
+    torch.cuda.empty_cache()
+
+
+def test_gri53_vjp_65536_states(pj, mechs):
+    """53 species / 325 reactions, 65,536 states: g_phi of sampled states and
+    y; then cotangents that vanish outside the sample, so that g_theta is the
+    oracle's sum over the sample and every other state's g_phi is exactly 0."""
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m)
+    n = 65536
+    N1 = m.n_species + 1
+    phi_h, par_h = synth.make_states(m, n, 2018 + 4, synth.CONP)
+    uw_h, uT_h = synth.make_cotangents(m.n_species, n, 2018 + 4)
+    phi, par, uw, uT = (_dev(torch, a) for a in (phi_h, par_h, uw_h, uT_h))
+    idx = sample_states(n, 8, 11)
+    ps, qs, us, ts = phi_h[:, idx], par_h[idx], uw_h[:, idx], uT_h[idx]
+    g_ref, th_ref = oracle.vjp(m, synth.CONP, ps, qs, us, ts)
+    e_phi, e_th = oracle.vjp_envelope(m, synth.CONP, ps, qs, us, ts)
+    y_ref = oracle.outputs_y(m, synth.CONP, ps, qs)
+    stream = torch.cuda.current_stream()
+    y = torch.empty((N1, n), dtype=torch.float64, device="cuda")
+    g = torch.empty_like(y)
+    gt = torch.empty((m.n_reactions, 3), dtype=torch.float64, device="cuda")
+    w, wb = _work(torch, h, pj.PJ_OP_VJP, n)
+    pj.pj_vjp(h, synth.CONP, n, par, phi, n, uw, uT, y, g, gt, None, w, wb, stream)
+    check_close(_cols(torch, g, idx), g_ref, e_phi, RTOL_VJP, 1e-300, "g_phi, 64 ki states")
+    check_close(_cols(torch, y, idx), y_ref, y_envelope(m, synth.CONP, ps, qs), RTOL_SRC, ATOL_SRC, "y, 64 ki states")
+    # cotangents only on the sample
+    mask = np.zeros(n, dtype=bool)
+    mask[idx] = True
+    uw0, uT0 = np.where(mask[None, :], uw_h, 0.0), np.where(mask, uT_h, 0.0)
+    pj.pj_vjp(h, synth.CONP, n, par, phi, n, _dev(torch, uw0), _dev(torch, uT0), y, g, gt, None, w, wb, stream)
+    check_close(gt.cpu().numpy(), th_ref, e_th, RTOL_VJP, 1e-300, "g_theta over the sample, 64 ki states")
+    gn = g.cpu().numpy()
+    assert np.all(gn[:, ~mask] == 0.0)
+    check_close(gn[:, idx], g_ref, e_phi, RTOL_VJP, 1e-300, "g_phi with masked cotangents")
+
+
+def test_ic5874_ragged_batches_in_one_plan(pj, mechs):
+    """874 species / 3796 reactions, the 32 log-uniform batches (623,411
+    states) through one plan of persistent kernels in groups sharing an output
+    pool, replayed from a captured graph: source terms and sampled Jacobian
+    columns of states of several batches."""
+    import torch
+    m = mechs("ic5874")
+    h = pj.pj_mech_create(m)
+    N1 = m.n_species + 1
+    sizes = [int(x) for x in synth.ragged_batch_sizes()]
+    group_states = 140000
+    groups, cur, acc = [], [], 0
+    for b, nb in enumerate(sizes):
+        if cur and acc + nb > group_states:
+            groups.append(cur)
+            cur, acc = [], 0
+        cur.append(b)
+        acc += nb
+    groups.append(cur)
+    pool_states = max(sum(sizes[b] for b in g) for g in groups)
+    pool = torch.empty(pool_states * h.nnz, dtype=torch.float64, device="cuda")
+    fpool = torch.empty(pool_states * N1, dtype=torch.float64, device="cuda")
+    # the groups share the pool, so the last group's outputs are the ones
+    # left after the replay: its first and last batches are checked
+    last = groups[-1]
+    check = {last[0], last[-1]}
+    batches, host = [], {}
+    for g in groups:
+        off = 0
+        for b in g:
+            nb = sizes[b]
+            phi_h, par_h = synth.make_states(m, nb, 2018 + 5 + 7919 * b, synth.CONP)
+            if b in check:
+                host[b] = (phi_h, par_h)
+            o = pool[off * h.nnz:(off + nb) * h.nnz].view(h.nnz, nb)
+            f = fpool[off * N1:(off + nb) * N1].view(N1, nb)
+            batches.append((_dev(torch, par_h), _dev(torch, phi_h), o, f))
+            off += nb
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches, max_states_per_launch=group_states, status=status)
+    plan.set_config(128, 8, 0)
+    gs = torch.cuda.Stream()
+    plan.capture(gs)
+    plan.launch(gs)
+    gs.synchronize()
+    assert int(status.item()) == 0
+    rp, ci = h.sparsity(pj.PJ_CSR)
+    rows = np.repeat(np.arange(N1), np.diff(rp))
+    cols = [0, 1, 2, 300, 873]
+    for b in sorted(check):
+        phi_h, par_h = host[b]
+        _, _, o, f = batches[b]
+        idx = np.unique([0, 33, sizes[b] // 2, sizes[b] - 1])
+        ps, qs = phi_h[:, idx], par_h[idx]
+        ref, env = oracle.source_term_envelope(m, synth.CONP, ps, qs)
+        check_close(_cols(torch, f, idx), ref, env, RTOL_SRC, ATOL_SRC, f"874 species, batch {b}")
+        Jc = oracle.jacobian_columns(m, synth.CONP, ps, qs, cols)
+        dense = np.zeros((N1, N1, len(idx)))
+        dense[rows, ci] = _cols(torch, o, idx)
+        got = dense[:, cols]
+        scale = np.max(np.abs(Jc), axis=0, keepdims=True)
+        assert np.all(np.abs(got - Jc) <= RTOL_JAC * np.abs(Jc) + 1e-12 * scale), b
+    del plan, batches, pool, fpool
+    torch.cuda.empty_cache()

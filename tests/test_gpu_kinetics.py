@@ -36,7 +36,8 @@ def to_dev(a, ld=None):
     return buf[:, : a.shape[1]]
 
 
-SRC_CASES = [("all_kinds", 37), ("bath_efficiency", 33), ("all_types", 41), ("h2co13", 4096), ("gri53", 777), ("usc111", 301)]
+SRC_CASES = [("all_kinds", 37), ("bath_efficiency", 33), ("all_types", 41), ("h2co13", 4096), ("gri53", 777), ("gri53_types", 333),
+               ("usc111", 301)]
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
@@ -50,7 +51,8 @@ def test_source_terms_match_oracle(pj, mechs, name, n, mode):
     check_close(out, ref, env, RTOL_SRC, ATOL_SRC, f"{name} mode={mode}")
 
 
-JAC_CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("all_types", 36), ("h2co13", 200), ("gri53", 70), ("usc111", 20)]
+JAC_CASES = [("all_kinds", 40), ("bath_efficiency", 35), ("all_types", 36), ("h2co13", 200), ("gri53", 70), ("gri53_types", 45),
+             ("usc111", 20)]
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
@@ -160,3 +162,18 @@ def test_jacobian_requires_source_term_buffer(pj, mechs):
     with pytest.raises(pj.PJError) as e:
         pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, 8, d_par, d_phi, 8, vals, None)
     assert e.value.code == N.PJ_ERR_ARG
+
+
+def test_mechanism_file_gives_identical_results(pj, mechs, tmp_path):
+    """A mechanism loaded from its text file evaluates bit for bit like the
+    one created from arrays (every reaction type)."""
+    import torch
+    m = mechs("gri53_types")
+    path = str(tmp_path / "types.pjmech")
+    synth.write_mechanism(m, path)
+    h1, h2 = pj.pj_mech_create(m), pj.pj_mech_load(path)
+    for mode in (synth.CONP, synth.CONV):
+        phi, par = synth.make_states(m, 300, 4 + mode, mode)
+        d_phi, d_par = to_dev(phi), to_dev(par)
+        assert torch.equal(pj.source_terms(h1, mode, d_phi, d_par), pj.source_terms(h2, mode, d_phi, d_par))
+        assert torch.equal(pj.jacobian_sparse(h1, mode, d_phi, d_par), pj.jacobian_sparse(h2, mode, d_phi, d_par))

@@ -43,7 +43,7 @@ def _mech(mechs, name):
 
 
 @pytest.mark.parametrize("from_j", [False, True])
-@pytest.mark.parametrize("name,n", [("all_kinds", 30), ("all_types", 20), ("h2co13", 100), ("gri53", 40), ("usc111", 12)])
+@pytest.mark.parametrize("name,n", [("all_kinds", 30), ("all_types", 20), ("h2co13", 100), ("gri53", 40), ("gri53_types", 30), ("usc111", 12)])
 def test_lu_fp64_newton_matrices(pj, mechs, name, n, from_j):
     import torch
     m = _mech(mechs, name)

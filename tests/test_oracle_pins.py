@@ -176,7 +176,7 @@ def test_sri_reduces_to_lindemann_and_unit_pr():
 
 
 # ------------------------------------------------- conservation laws ----
-@pytest.mark.parametrize("name", ["h2co13", "gri53", "usc111"])
+@pytest.mark.parametrize("name", ["h2co13", "gri53", "gri53_types", "usc111"])
 def test_element_and_mass_conservation(mechs, name):
     m = mechs(name)
     phi, par = synth.make_states(m, 64, 5, synth.CONP)
@@ -190,7 +190,7 @@ def test_element_and_mass_conservation(mechs, name):
     assert np.all(np.abs(mass) <= 64 * U * (np.abs(m.W) @ np.abs(w)))
 
 
-@pytest.mark.parametrize("name", ["h2co13", "gri53"])
+@pytest.mark.parametrize("name", ["h2co13", "gri53", "gri53_types"])
 def test_conp_conv_share_production_rates(mechs, name):
     m = mechs(name)
     pc, parc = synth.make_states(m, 32, 9, synth.CONP)
@@ -207,7 +207,7 @@ def _directional(fun, phi, direction, h=1e-30):
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("name", ["h2co13", "gri53"])
+@pytest.mark.parametrize("name", ["h2co13", "gri53", "gri53_types"])
 def test_energy_and_mass_conserved_along_source_terms(mechs, name, mode):
     """Adiabatic closed system: total enthalpy (CONP) or internal energy (CONV)
     and total mass, with the bath gas from the ideal-gas law, are constant
@@ -320,7 +320,7 @@ def test_jacobian_closed_form_first_order():
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
-@pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "h2co13", "gri53"])
+@pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "h2co13", "gri53", "gri53_types"])
 def test_jacobian_matches_central_differences(mechs, mk, mode):
     m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency", "all_types") else mechs(mk)
     # no vanishing mole fractions, so a relative step of 1e-6 balances the
@@ -342,7 +342,7 @@ def test_jacobian_matches_central_differences(mechs, mk, mode):
         assert np.all(err <= tol), (j, np.max(err / tol))
 
 
-@pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "h2co13", "gri53"])
+@pytest.mark.parametrize("mk", ["all_kinds", "bath_efficiency", "all_types", "h2co13", "gri53", "gri53_types"])
 def test_pattern_superset_and_tight(mechs, mk):
     m = getattr(tm, mk)() if mk in ("all_kinds", "bath_efficiency", "all_types") else mechs(mk)
     mask = K.sparsity_pattern(m)

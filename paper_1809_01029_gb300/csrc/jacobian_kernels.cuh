@@ -15,7 +15,7 @@
 namespace pj {
 
 template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL>
-__global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const double* __restrict__ param,
+__global__ void __launch_bounds__(128, kJacRegCtas) k_jacobian(DevMech m, int64_t n, const double* __restrict__ param,
                                                   const double* __restrict__ phi, int64_t ld,
                                                   DT* __restrict__ J, double* __restrict__ dphi,
                                                   int* status, double* ws, int64_t ws_stride,
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) k_jacobian(DevMech m, int64_t n, const do
 // first SPLIT of them sit in shared memory, the rest in a global workspace
 // of ws_stride threads (the grid then covers exactly ws_stride threads).
 template <int MODE, int FMT, typename DT, bool NEWTON, int SPLIT, bool SPECIAL>
-__global__ void __launch_bounds__(128) k_jacobian_tm(DevMech m, int64_t n, const double* __restrict__ param,
+__global__ void __launch_bounds__(128, kJacRegCtas) k_jacobian_tm(DevMech m, int64_t n, const double* __restrict__ param,
                                                      const double* __restrict__ phi, int64_t ld,
                                                      DT* __restrict__ J, double* __restrict__ dphi, int* status,
                                                      const double* __restrict__ hstep, double gamma,

@@ -8,12 +8,16 @@
 // whose factors are not all finite (a zero or non-finite pivot, or overflow,
 // which FP32's range allows on stiff states) is counted in *status.
 //
-//  * Factorisation: one state per block.  M is scattered into a dense N x N
-//    array (pivot order) in shared memory -- or, when N^2 does not fit, in a
-//    per-block slice of a global workspace -- and eliminated pivot by pivot
-//    with the per-pivot lists of column rows and row columns: the block's
-//    threads tile the |rows| x |cols| update (threads over columns, keeping
-//    U_kj in a register, and over rows).  The factors are gathered into the
+//  * Factorisation: S states per block (S = 2 or 4 when S dense matrices
+//    still leave two blocks per SM, else 1).  M is scattered into a dense
+//    N x N array (pivot order) in shared memory -- interleaved over the
+//    block's states, so that one vector access moves an entry of all S -- or,
+//    when N^2 does not fit, one state per block in a per-block slice of a
+//    global workspace, and eliminated pivot by pivot with the per-pivot lists
+//    of column rows and row columns: the block's threads tile the
+//    |rows| x |cols| update, each pair (i, j) for all S states at once (the
+//    index work and the loop are shared by the S states, whose fused
+//    multiply-adds are independent).  The factors are gathered into the
 //    storage order.
 //  * Solve: one state per thread, streaming the factors in storage order
 //    (coalesced across the warp), forward substitution then backward; the
@@ -32,8 +36,62 @@ __device__ __forceinline__ T fma_t(T a, T b, T c) { return fma(a, b, c); }
 template <>
 __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
+// finiteness and zero tests on the bit pattern (integer instructions; the
+// FP64 pipe is the bound of the factorisation)
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+  return (__double_as_longlong(v) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool nonfinite_bits(float v) { return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u; }
+__device__ __forceinline__ bool zero_bits(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool zero_bits(float v) { return (__float_as_uint(v) << 1) == 0u; }
+
 template <typename T>
-__device__ __forceinline__ bool bad_pivot(T p) { return !(p != T(0)) || !isfinite(p); }
+__device__ __forceinline__ bool bad_pivot(T p) { return zero_bits(p) || nonfinite_bits(p); }
+
+// S values of one entry, one per state of the block, moved as one vector
+template <typename T, int S>
+struct LuVec;
+template <>
+struct LuVec<double, 2> {
+  using V = double2;
+};
+template <>
+struct LuVec<float, 2> {
+  using V = float2;
+};
+template <>
+struct LuVec<float, 4> {
+  using V = float4;
+};
+
+template <typename V>
+__device__ __forceinline__ V v_fms(V l, V u, V v);  // v - l u per component
+template <>
+__device__ __forceinline__ double2 v_fms(double2 l, double2 u, double2 v) {
+  return make_double2(fma(-l.x, u.x, v.x), fma(-l.y, u.y, v.y));
+}
+template <>
+__device__ __forceinline__ float2 v_fms(float2 l, float2 u, float2 v) {
+  return make_float2(fmaf(-l.x, u.x, v.x), fmaf(-l.y, u.y, v.y));
+}
+template <>
+__device__ __forceinline__ float4 v_fms(float4 l, float4 u, float4 v) {
+  return make_float4(fmaf(-l.x, u.x, v.x), fmaf(-l.y, u.y, v.y), fmaf(-l.z, u.z, v.z), fmaf(-l.w, u.w, v.w));
+}
+template <typename V>
+__device__ __forceinline__ V v_mul(V a, V b);
+template <>
+__device__ __forceinline__ double2 v_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+template <>
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) {
+  return make_float2(a.x * b.x, a.y * b.y);
+}
+template <>
+__device__ __forceinline__ float4 v_mul(float4 a, float4 b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
 
 // vals: CSR values of M (FROM_J = false) or of J (FROM_J: M = I - h gamma J
 // formed on the way in, h per state).
@@ -155,11 +213,138 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
     }
     for (int e = tid; e < L.lu_nnz; e += nt) {
       const T v = A[__ldg(L.l2d + e)];
-      if (!isfinite(v)) bad = 1;  // overflow anywhere (FP32 range) marks the state
+      if (nonfinite_bits(v)) bad = 1;  // overflow anywhere (FP32 range) marks the state
       lu[(int64_t)e * ld + s] = v;
     }
     __syncthreads();
     if (tid == 0 && bad && status) atomicAdd(status, 1);
+    __syncthreads();
+  }
+}
+
+// S states per block, the dense matrices interleaved in shared memory:
+// A[p] holds entry p (pivot-order dense position) of the block's S states.
+// The elimination is that of k_lu_factor, value for value, for each state; a
+// group's padding states (n not a multiple of S) factor the identity and are
+// neither written nor counted.
+template <typename T, int S, bool FROM_J>
+__global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T* __restrict__ vals, int64_t ld,
+                                                     const double* __restrict__ hstep, double gamma,
+                                                     T* __restrict__ lu, int* status) {
+  using V = typename LuVec<T, S>::V;
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  V* A = reinterpret_cast<V*>(lu_smem);
+  const int N = L.N, tid = threadIdx.x, nt = blockDim.x;
+  const int NN = N * N;
+  __shared__ int bad[S];
+  __shared__ V s_inv;
+  __shared__ T s_hg[S];
+  auto at = [&](int p, int q) -> T& { return reinterpret_cast<T*>(A + p)[q]; };
+  const int64_t groups = (n + S - 1) / S;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t s0 = g * S;
+    const int live = (int)(n - s0 < S ? n - s0 : S);
+    if (tid < S) {
+      bad[tid] = 0;
+      s_hg[tid] = FROM_J && tid < live ? T(-hstep[s0 + tid] * gamma) : T(0);
+    }
+    for (int p = tid; p < NN * S; p += nt) reinterpret_cast<T*>(A)[p] = T(0);
+    __syncthreads();
+    // consecutive threads take the S states of one entry (adjacent in vals)
+    for (int t = tid; t < L.nnz * S; t += nt) {
+      const int e = t / S, q = t - e * S;
+      if (q < live) {
+        const T v = vals[(int64_t)e * ld + s0 + q];
+        at(__ldg(L.m2d + e), q) = FROM_J ? s_hg[q] * v : v;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < N * S; t += nt) {
+      const int k = t / S, q = t - k * S;
+      if (FROM_J || q >= live) at(k * N + k, q) += T(1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < S; q++) {
+        const T piv = at(0, q);
+        if (bad_pivot(piv)) bad[q] = 1;
+        reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < N; k++) {
+      const V inv = s_inv;
+      const int r0 = __ldg(L.rptr + k), nr = __ldg(L.rptr + k + 1) - r0;
+      const int c0 = __ldg(L.cptr + k), nc = __ldg(L.cptr + k + 1) - c0;
+      for (int a = tid; a < nr; a += nt) {
+        const int i = __ldg(L.ridx + r0 + a);
+        A[i * N + k] = v_mul(A[i * N + k], inv);
+      }
+      __syncthreads();
+      // the nr x nc update flattened over the block: pair p = a * nc + c,
+      // stride nt, four pairs at a time (distinct pairs touch distinct
+      // entries, so their loads go out first)
+      const int tot = nr * nc;
+      if (tid < tot) {
+        const int di = nt / nc, dj = nt - di * nc;
+        int ia = tid / nc, jc = tid - ia * nc;
+        auto step = [&]() {
+          ia += di;
+          jc += dj;
+          if (jc >= nc) {
+            jc -= nc;
+            ia++;
+          }
+        };
+        int p = tid;
+        for (; p + 3 * nt < tot; p += 4 * nt) {
+          const int i0 = __ldg(L.ridx + r0 + ia), j0 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i1 = __ldg(L.ridx + r0 + ia), j1 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i2 = __ldg(L.ridx + r0 + ia), j2 = __ldg(L.cidx + c0 + jc);
+          step();
+          const int i3 = __ldg(L.ridx + r0 + ia), j3 = __ldg(L.cidx + c0 + jc);
+          step();
+          const V l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
+          const V u0 = A[k * N + j0], u1 = A[k * N + j1], u2 = A[k * N + j2], u3 = A[k * N + j3];
+          const V v0 = A[i0 * N + j0], v1 = A[i1 * N + j1], v2 = A[i2 * N + j2], v3 = A[i3 * N + j3];
+          A[i0 * N + j0] = v_fms(l0, u0, v0);
+          A[i1 * N + j1] = v_fms(l1, u1, v1);
+          A[i2 * N + j2] = v_fms(l2, u2, v2);
+          A[i3 * N + j3] = v_fms(l3, u3, v3);
+        }
+        for (; p < tot; p += nt) {
+          const int i = __ldg(L.ridx + r0 + ia), j = __ldg(L.cidx + c0 + jc);
+          A[i * N + j] = v_fms(A[i * N + k], A[k * N + j], A[i * N + j]);
+          step();
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
+        if (k + 1 < N) {
+#pragma unroll
+          for (int q = 0; q < S; q++) {
+            const T piv = at((k + 1) * N + k + 1, q);
+            if (bad_pivot(piv)) bad[q] = 1;
+            reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < L.lu_nnz * S; t += nt) {
+      const int e = t / S, q = t - e * S;
+      if (q < live) {
+        const T v = at(__ldg(L.l2d + e), q);
+        if (nonfinite_bits(v)) bad[q] = 1;
+        lu[(int64_t)e * ld + s0 + q] = v;
+      }
+    }
+    __syncthreads();
+    if (tid < live && bad[tid] && status) atomicAdd(status, 1);
     __syncthreads();
   }
 }
@@ -212,6 +397,7 @@ __global__ void __launch_bounds__(128) k_lu_solve(DevLu L, int64_t n, const T* _
 // ---------------------------------------------------------------------------
 struct LuPlan {
   bool smem;        // dense matrix in shared memory
+  int S;            // states per block (1, 2 or 4; shared-memory plans only)
   int threads;      // per block
   int grid;         // persistent blocks
   size_t dyn;       // shared memory per block
@@ -224,15 +410,26 @@ static LuPlan lu_plan(int N, size_t esize, int64_t n) {
   const int64_t states = std::max<int64_t>(n, 1);
   if (dense <= kSmemCap) {
     p.smem = true;
-    p.dyn = dense;
-    const int ctas = std::max(1, std::min(16, (int)(kSmemPerSm / (dense + 1024 + 256))));
+    // the most states per block (16-byte vectors: 2 FP64, 4 FP32) that still
+    // leave two blocks per SM
+    p.S = 1;
+    for (int S : {4, 2}) {
+      if (S * esize > 16) continue;
+      if (2 * (S * dense + 1024 + 256) <= kSmemPerSm && S * dense <= kSmemCap) {
+        p.S = S;
+        break;
+      }
+    }
+    p.dyn = dense * p.S;
+    const int ctas = std::max(1, std::min(16, (int)(kSmemPerSm / (p.dyn + 1024 + 256))));
     int warps = (16 + ctas - 1) / ctas;  // at least 16 warps per SM
     warps = std::max(1, std::min(8, warps));
     p.threads = 32 * warps;
-    p.grid = (int)std::min<int64_t>(states, (int64_t)sm_count() * ctas);
+    p.grid = (int)std::min<int64_t>((states + p.S - 1) / p.S, (int64_t)sm_count() * ctas);
     p.ws_bytes = 0;
   } else {
     p.smem = false;
+    p.S = 1;
     p.dyn = 0;
     p.threads = 256;
     p.grid = (int)std::min<int64_t>(states, (int64_t)sm_count() * 2);
@@ -253,6 +450,19 @@ static int launch_factor_t(const DevLu& L, int64_t n, const void* vals, int64_t 
     return fail(PJ_ERR_NOMEM, "workspace too small for the LU factorisation (see pj_workspace_size)");
   T* gws = p.smem ? nullptr : static_cast<T*>(work);
   int rc;
+  if (p.S > 1) {
+    auto pick = [&](auto kern) -> int {
+      int r;
+      if ((r = set_smem(kern, p.dyn))) return r;
+      kern<<<p.grid, p.threads, p.dyn, st>>>(L, n, static_cast<const T*>(vals), ld, hstep, gamma,
+                                             static_cast<T*>(lu), status);
+      return check_cuda(cudaGetLastError(), "k_lu_factor_v launch");
+    };
+    if constexpr (sizeof(T) == 4) {
+      if (p.S == 4) return hstep ? pick(k_lu_factor_v<T, 4, true>) : pick(k_lu_factor_v<T, 4, false>);
+    }
+    return hstep ? pick(k_lu_factor_v<T, 2, true>) : pick(k_lu_factor_v<T, 2, false>);
+  }
   if (hstep) {
     auto kern = k_lu_factor<T, true>;
     if ((rc = set_smem(kern, p.dyn))) return rc;

@@ -51,6 +51,10 @@ __device__ __forceinline__ bool bad_pivot(T p) { return zero_bits(p) || nonfinit
 // S values of one entry, one per state of the block, moved as one vector
 template <typename T, int S>
 struct LuVec;
+template <typename T>
+struct LuVec<T, 1> {
+  using V = T;
+};
 template <>
 struct LuVec<double, 2> {
   using V = double2;
@@ -67,6 +71,14 @@ struct LuVec<float, 4> {
 template <typename V>
 __device__ __forceinline__ V v_fms(V l, V u, V v);  // v - l u per component
 template <>
+__device__ __forceinline__ double v_fms(double l, double u, double v) {
+  return fma(-l, u, v);
+}
+template <>
+__device__ __forceinline__ float v_fms(float l, float u, float v) {
+  return fmaf(-l, u, v);
+}
+template <>
 __device__ __forceinline__ double2 v_fms(double2 l, double2 u, double2 v) {
   return make_double2(fma(-l.x, u.x, v.x), fma(-l.y, u.y, v.y));
 }
@@ -80,6 +92,14 @@ __device__ __forceinline__ float4 v_fms(float4 l, float4 u, float4 v) {
 }
 template <typename V>
 __device__ __forceinline__ V v_mul(V a, V b);
+template <>
+__device__ __forceinline__ double v_mul(double a, double b) {
+  return a * b;
+}
+template <>
+__device__ __forceinline__ float v_mul(float a, float b) {
+  return a * b;
+}
 template <>
 __device__ __forceinline__ double2 v_mul(double2 a, double2 b) {
   return make_double2(a.x * b.x, a.y * b.y);
@@ -226,7 +246,10 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
 // A[p] holds entry p (pivot-order dense position) of the block's S states.
 // The elimination is that of k_lu_factor, value for value, for each state; a
 // group's padding states (n not a multiple of S) factor the identity and are
-// neither written nor counted.
+// neither written nor counted.  Two barriers per pivot: the reciprocal of the
+// next pivot is formed by thread 0 during the update (the next pivot's entry
+// is final once pair 0 of the update, the only one that can change it, is
+// done), overlapping the other threads' updates.
 template <typename T, int S, bool FROM_J>
 __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T* __restrict__ vals, int64_t ld,
                                                      const double* __restrict__ hstep, double gamma,
@@ -286,9 +309,27 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
       // stride nt, four pairs at a time (distinct pairs touch distinct
       // entries, so their loads go out first)
       const int tot = nr * nc;
-      if (tid < tot) {
+      int p = tid;
+      if (tid == 0) {
+        A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
+        if (k + 1 < N) {
+          // rows and columns ascend, so entry (k+1, k+1) can only be pair 0
+          const int d = (k + 1) * N + k + 1;
+          if (tot > 0 && __ldg(L.ridx + r0) == k + 1 && __ldg(L.cidx + c0) == k + 1) {
+            A[d] = v_fms(A[d - 1], A[k * N + k + 1], A[d]);
+            p = nt;
+          }
+#pragma unroll
+          for (int q = 0; q < S; q++) {
+            const T piv = at(d, q);
+            if (bad_pivot(piv)) bad[q] = 1;
+            reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
+          }
+        }
+      }
+      if (p < tot) {
         const int di = nt / nc, dj = nt - di * nc;
-        int ia = tid / nc, jc = tid - ia * nc;
+        int ia = p / nc, jc = p - ia * nc;
         auto step = [&]() {
           ia += di;
           jc += dj;
@@ -297,7 +338,6 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
             ia++;
           }
         };
-        int p = tid;
         for (; p + 3 * nt < tot; p += 4 * nt) {
           const int i0 = __ldg(L.ridx + r0 + ia), j0 = __ldg(L.cidx + c0 + jc);
           step();
@@ -319,18 +359,6 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
           const int i = __ldg(L.ridx + r0 + ia), j = __ldg(L.cidx + c0 + jc);
           A[i * N + j] = v_fms(A[i * N + k], A[k * N + j], A[i * N + j]);
           step();
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
-        if (k + 1 < N) {
-#pragma unroll
-          for (int q = 0; q < S; q++) {
-            const T piv = at((k + 1) * N + k + 1, q);
-            if (bad_pivot(piv)) bad[q] = 1;
-            reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
-          }
         }
       }
       __syncthreads();
@@ -450,7 +478,7 @@ static int launch_factor_t(const DevLu& L, int64_t n, const void* vals, int64_t 
     return fail(PJ_ERR_NOMEM, "workspace too small for the LU factorisation (see pj_workspace_size)");
   T* gws = p.smem ? nullptr : static_cast<T*>(work);
   int rc;
-  if (p.S > 1) {
+  if (p.smem) {
     auto pick = [&](auto kern) -> int {
       int r;
       if ((r = set_smem(kern, p.dyn))) return r;
@@ -461,7 +489,8 @@ static int launch_factor_t(const DevLu& L, int64_t n, const void* vals, int64_t 
     if constexpr (sizeof(T) == 4) {
       if (p.S == 4) return hstep ? pick(k_lu_factor_v<T, 4, true>) : pick(k_lu_factor_v<T, 4, false>);
     }
-    return hstep ? pick(k_lu_factor_v<T, 2, true>) : pick(k_lu_factor_v<T, 2, false>);
+    if (p.S == 2) return hstep ? pick(k_lu_factor_v<T, 2, true>) : pick(k_lu_factor_v<T, 2, false>);
+    return hstep ? pick(k_lu_factor_v<T, 1, true>) : pick(k_lu_factor_v<T, 1, false>);
   }
   if (hstep) {
     auto kern = k_lu_factor<T, true>;

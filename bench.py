@@ -191,7 +191,7 @@ def lu_work_per_state(h):
 # hash of the kernel sources at capture time; a number is only used while
 # the sources are unchanged.
 PROFILE_OF = {("jac_csr", "gri53"): "k_jacobian_tm_gri53.md", ("source", "gri53"): "k_source_terms_gri53.md",
-              ("lu", "gri53"): "k_lu_factor_gri53.md"}
+              ("lu", "gri53"): "k_lu_factor_gri53.md", ("ragged", "ic5874"): "k_batched_ic5874.md"}
 
 
 def sources_hash():
@@ -373,14 +373,16 @@ def types_workload(pj, synth, torch, dev, stream):
     return out
 
 
-def ragged_workload(pj, synth, torch, dev, stream, group_states=140000):
+def build_ragged(pj, synth, torch, dev, stream, scale=1.0, config=None, group_states=140000):
     """874 species / 3796 reactions, 32 log-uniform batches of 1,024..65,536
-    states: source terms + CSR Jacobian through one plan (persistent kernels,
-    groups of <= group_states states sharing one output pool), autotuned on a
-    sample, captured as a CUDA graph and timed by replay."""
+    states (each scaled by `scale`, at least 1): source terms + CSR Jacobian
+    through one plan (persistent kernels, groups of <= group_states states
+    sharing one output pool), autotuned on the first six batches unless
+    `config` (threads per block, blocks per SM, shared) is given, captured as
+    a CUDA graph on its own stream."""
     m = synth.make_mechanism("ic5874")
     h = pj.pj_mech_create(m)
-    sizes = [int(x) for x in synth.ragged_batch_sizes()]
+    sizes = [max(1, int(int(x) * scale)) for x in synth.ragged_batch_sizes()]
     N1 = m.n_species + 1
     # group assignment as the plan does it (consecutive batches)
     groups, cur, acc = [], [], 0
@@ -406,23 +408,34 @@ def ragged_workload(pj, synth, torch, dev, stream, group_states=140000):
             batches.append((par, phi, o, f))
             off += n
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    cache = os.path.join(tempfile.gettempdir(), "pyjac_gb_autotune.jsonl")
-    sample = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches[:6], status=status)
-    cfg = sample.autotune(stream=stream, cache_path=cache, reps=1)
-    del sample
+    if config is None:
+        cache = os.path.join(tempfile.gettempdir(), "pyjac_gb_autotune.jsonl")
+        sample = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches[:6], status=status)
+        cfg = sample.autotune(stream=stream, cache_path=cache, reps=1)
+        del sample
+        config = (cfg["threads_per_block"], cfg["blocks_per_sm"], cfg["use_shared"])
     plan = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches, max_states_per_launch=group_states, status=status)
-    plan.set_config(cfg["threads_per_block"], cfg["blocks_per_sm"], cfg["use_shared"])
+    plan.set_config(*config)
     gs = torch.cuda.Stream(dev)
     plan.capture(gs)
+    return {"m": m, "h": h, "plan": plan, "stream": gs, "status": status, "sizes": sizes, "groups": groups,
+            "total": sum(sizes), "keep": (batches, pool, fpool)}
+
+
+def ragged_workload(pj, synth, torch, dev, stream):
+    """States/s of the 874-species ragged workload (see build_ragged), timed
+    by graph replay."""
+    r = build_ragged(pj, synth, torch, dev, stream)
+    plan, gs = r["plan"], r["stream"]
     plan.launch(gs)
     gs.synchronize()
     t = _time(torch, gs, lambda: plan.launch(gs), reps=2)
-    assert int(status.item()) == 0
-    total = sum(sizes)
+    assert int(r["status"].item()) == 0
+    total = r["total"]
     res = {"ic5874_ragged_jacobian_csr_graph": total / (t * 1e-3),
-           "ic5874_ragged_info": {"batches": len(sizes), "states": total, "groups": len(groups),
+           "ic5874_ragged_info": {"batches": len(r["sizes"]), "states": total, "groups": len(r["groups"]),
                                   "config": plan.config(), "ms_per_replay": t}}
-    del plan, batches, pool, fpool
+    del plan, r
     torch.cuda.empty_cache()
     return res
 
@@ -451,6 +464,68 @@ def run_reference(args, rank, world):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_ragged(args, rank, world, local, torch, dist, synth, pj):
+    """--op ragged: one step is one replay of the 874-species ragged plan
+    (all 32 batches, or --n states in the same proportions)."""
+    from paper_1809_01029_gb300 import replicas
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    scale = args.n / 623411.0 if args.n else 1.0
+    cfg = tuple(int(x) for x in args.ragged_config.split(",")) if args.ragged_config else None
+    r = build_ragged(pj, synth, torch, dev, stream, scale=scale, config=cfg)
+    plan, gs, n, m = r["plan"], r["stream"], r["total"], r["m"]
+    for _ in range(args.warmup):
+        plan.launch(gs)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk_dir = args.clocks_dir or tempfile.gettempdir()
+    os.makedirs(clk_dir, exist_ok=True)
+    clk_path = os.path.join(clk_dir, f"bench_clocks_r{rank}.csv")
+    clk = sample_clocks_start(clk_path)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(gs)
+    for _ in range(args.steps):
+        plan.launch(gs)
+    e1.record(gs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sample_clocks_stop(clk, clk_path, local)
+    if world > 1:
+        dist.barrier()
+    ms_max = replicas.max_over_ranks(ms, dist if world > 1 else None)
+    assert int(r["status"].item()) == 0, "invalid states in the benchmark batches"
+    fp64_work = fp64_work_per_state(m)
+    achieved = fp64_work * n / (ms * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_batched", "work_per_state": fp64_work,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
+    tr = kernel_traffic("ragged", "ic5874")
+    if tr is not None:
+        roofline["traffic"] = tr * n
+        roofline["traffic_source"] = "ncu dram bytes per state of the current kernel sources x states"
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n * world / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ic5874_ragged", "mechanism": "synthetic 874 species / 3796 reactions (seed %d)"
+                       % synth.SPECS["ic5874"].seed, "states_per_gpu": n, "batches": len(r["sizes"]),
+                       "groups": len(r["groups"]), "plan": plan.config(), "mode": "CONP", "op": "ragged",
+                       "output": "source terms + CSR Jacobian (nnz %d) per batch, CUDA-graph replay" % r["h"].nnz,
+                       "l2": "outputs larger than L2", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": None, "e2e": None, "clocks": clocks,
+            "gpu_launches": args.steps * len(r["groups"]), "variants": {}}))
+    del plan, r
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,8 +538,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi clock samples (default: a temp dir)")
     ap.add_argument("--op", default="jac_csr",
-                    choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp", "lu"],
+                    choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp", "lu", "ragged"],
                     help="what one step evaluates (default: source terms + CSR Jacobian)")
+    ap.add_argument("--ragged-config", default=None,
+                    help="ragged op: threads_per_block,blocks_per_sm,use_shared instead of autotuning")
     ap.add_argument("--mode", default="conp", choices=["conp", "conv"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -484,6 +561,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     pj.load_library()
+    if args.op == "ragged":
+        return run_ragged(args, rank, world, local, torch, dist, synth, pj)
     mech_name = {"newton": "usc111"}.get(args.op, "gri53")
     default_n = {"newton": 262144, "vjp": 65536, "lu": 262144}.get(args.op, 1048576)
     m = synth.make_mechanism(mech_name)
@@ -670,9 +749,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = oracle_baseline(m, mode, CPU_SAMPLE, 2018 + 2)
+        n_cpu = CPU_SAMPLE if mech_name == "gri53" else CPU_SAMPLE // 4
+        v, dt = oracle_baseline(m, mode, n_cpu, 2018 + 2)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{CPU_SAMPLE} states of the {WORKLOAD} workload: numpy source terms + complex-step CSR Jacobian "
+               "sample": f"{n_cpu} states of the {m.name} mechanism: numpy source terms + complex-step CSR Jacobian "
                          f"({dt:.1f} s)"}
 
     if rank == 0:
@@ -694,7 +774,7 @@ def main():
                        "l2": "inputs and outputs larger than L2 (%.1f GB per step)" % ((h.nnz + 2 * (m.n_species + 1)) * n * 8 / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps, "variants": variants}))
+            "gpu_launches": args.steps * (2 if args.op == "vjp" else 1), "variants": variants}))
     if world > 1:
         dist.destroy_process_group()
 

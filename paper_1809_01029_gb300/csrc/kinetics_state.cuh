@@ -378,10 +378,19 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
 
     const int row_lo = __ldg(&r->row_lo), row_hi = __ldg(&r->row_hi);
     const DT VdqdT = V_t * dqdT, VdqdS = V_t * dqdS;
+    // sparse targets in the order of the reaction's target list (the host
+    // builds it in exactly the order of the contributions below); dense
+    // positions are plain arithmetic
+    const int32_t* tg = FMT == PJ_CSR ? m.tgt_csr + __ldg(&r->tgt_lo) : m.tgt_csc + __ldg(&r->tgt_lo);
+    auto target = [&](int row, int col) -> int64_t {
+      if (FMT == PJ_DENSE) return (int64_t)row * m.N + col;
+      return __ldg(tg++);
+    };
     for (int q2 = row_lo; q2 < row_hi; q2++) {
       const RowNu rn = m.rows[q2];
-      if (w) jred(J, jpos<FMT>(m, rn.k + 2, 0), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdT));
-      if (w) jred(J, jpos<FMT>(m, rn.k + 2, 1), ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
+      const int64_t e0 = target(rn.k + 2, 0), e1 = target(rn.k + 2, 1);
+      if (w) jred(J, e0, ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdT));
+      if (w) jred(J, e1, ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
     }
 
     // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i
@@ -393,10 +402,12 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
       }
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
-        if (w) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, nu_times_t<DT>(rn.nu, rn.nud, val));
+        const int64_t e = target(rn.k + 2, j + 2);
+        if (w) jred(J, e, ld, s, nu_times_t<DT>(rn.nu, rn.nud, val));
       }
-      if (w) jred(J, jpos<FMT>(m, 0, j + 2), ld, s, dE * val);
-      if (w) jred(J, jpos<FMT>(m, 1, j + 2), ld, s, dW * val);
+      const int64_t eT = target(0, j + 2), eS = target(1, j + 2);
+      if (w) jred(J, eT, ld, s, dE * val);
+      if (w) jred(J, eS, ld, s, dW * val);
     };
 #pragma unroll
     for (int a = 0; a < PJ_MAX_SP; a++) {

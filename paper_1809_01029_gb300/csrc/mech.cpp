@@ -387,6 +387,38 @@ int mech_build(pj_mech* m) {
     if (!ok) return fail(PJ_ERR_MECH, "internal: the sparsity pattern misses an entry the Jacobian kernel writes");
   }
 
+  // The sparse targets of each reaction's Jacobian contributions, in the
+  // order jacobian_state makes them: per row it changes the T and S columns;
+  // then per slot (reactant a, reversible product a, a = 0, 1, ..., then the
+  // non-unit efficiencies), skipping the bath gas, its column in each row and
+  // in rows T and S.  Read sequentially by the kernels instead of looking up
+  // the N x N index map per contribution.
+  std::vector<int32_t> tgt_csr, tgt_csc;
+  for (int q = 0; q < nr; q++) {
+    Rxn& r = rx[q];
+    r.tgt_lo = (int32_t)tgt_csr.size();
+    auto push = [&](int i, int j) {
+      tgt_csr.push_back(m->pos_csr[(size_t)i * N + j]);
+      tgt_csc.push_back(m->pos_csc[(size_t)i * N + j]);
+    };
+    for (int q2 = r.row_lo; q2 < r.row_hi; q2++) {
+      push(rows[q2].k + 2, 0);
+      push(rows[q2].k + 2, 1);
+    }
+    auto slot = [&](int j) {
+      if (j == bath) return;
+      for (int q2 = r.row_lo; q2 < r.row_hi; q2++) push(rows[q2].k + 2, j + 2);
+      push(0, j + 2);
+      push(1, j + 2);
+    };
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < r.nreac) slot(r.sp[a]);
+      if (r.rev && a < r.nprod) slot(r.sp[PJ_MAX_SP + a]);
+    }
+    if (has_third_body(r.kind))
+      for (int e = r.eff_lo; e < r.eff_hi; e++) slot(eff_sp[e]);
+  }
+
   // one device allocation holding every constant array
   const size_t o_nasa = 0;
   const size_t o_wfac = align256(o_nasa + nasa.size() * sizeof(double));
@@ -399,7 +431,9 @@ int mech_build(pj_mech* m) {
   const size_t o_perm = align256(o_pcsc + (size_t)N * N * sizeof(int32_t));
   const size_t o_etab = align256(o_perm + (size_t)nr * sizeof(int32_t));
   const size_t o_tab = align256(o_etab + 256 * sizeof(double));
-  const size_t total = align256(o_tab + tab.size() * sizeof(double));
+  const size_t o_tcsr = align256(o_tab + tab.size() * sizeof(double));
+  const size_t o_tcsc = align256(o_tcsr + tgt_csr.size() * sizeof(int32_t));
+  const size_t total = align256(o_tcsc + tgt_csc.size() * sizeof(int32_t));
   // 2^(j/256) in extended precision, rounded once to double
   double etab[256];
   for (int j = 0; j < 256; j++) etab[j] = (double)std::exp2((long double)j / 256.0L);
@@ -417,6 +451,8 @@ int mech_build(pj_mech* m) {
   put(o_perm, m->perm.data(), m->perm.size() * sizeof(int32_t));
   put(o_etab, etab, sizeof etab);
   put(o_tab, tab.data(), tab.size() * sizeof(double));
+  put(o_tcsr, tgt_csr.data(), tgt_csr.size() * sizeof(int32_t));
+  put(o_tcsc, tgt_csc.data(), tgt_csc.size() * sizeof(int32_t));
 
   // Without any CUDA device the handle stays host-only: its pattern can be
   // queried, evaluation calls fail with PJ_ERR_CUDA.
@@ -455,6 +491,8 @@ int mech_build(pj_mech* m) {
   dm.perm = reinterpret_cast<const int32_t*>(b + o_perm);
   dm.exp_tab = reinterpret_cast<const double*>(b + o_etab);
   dm.tab = reinterpret_cast<const double*>(b + o_tab);
+  dm.tgt_csr = reinterpret_cast<const int32_t*>(b + o_tcsr);
+  dm.tgt_csc = reinterpret_cast<const int32_t*>(b + o_tcsc);
   dm.has_pdep = has_pdep ? 1 : 0;
   dm.nr_plain = nr_plain;
   return lu_build(m);

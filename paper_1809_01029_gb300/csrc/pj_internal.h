@@ -57,6 +57,7 @@ struct alignas(8) Rxn {
   int32_t tab_lo;                 // DevMech::tab: explicit reverse (ln A, beta, theta) when rev == 2,
                                   // then the P-log entries / Chebyshev block
   int16_t tab_n, tab_m;           // P-log entries / Chebyshev N_T, N_P
+  int32_t tgt_lo;                 // first of this reaction's Jacobian targets in tgt_csr / tgt_csc
 };
 
 struct RowNu {
@@ -77,6 +78,8 @@ struct DevMech {
   const RowNu* rows;              // [n_rows]
   const int32_t* pos_csr;         // [N*N] full -> CSR value index, -1 if absent
   const int32_t* pos_csc;         // [N*N] full -> CSC value index, -1 if absent
+  const int32_t* tgt_csr;         // per reaction, the value indices its sparse contributions
+  const int32_t* tgt_csc;         //   go to, in the order the Jacobian kernels make them
   const int32_t* perm;            // [nr] kernel order -> original reaction index
   const double* exp_tab;          // [256] 2^(j/256), correctly rounded (pj_exp)
   const double* tab;              // P-log entries (ln P, ln A, beta, theta) and Chebyshev

@@ -240,7 +240,7 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
     const int rev = __ldg(&r->rev);
     double lnkinf, dlnkf_d, dlnP_d, dlnkinf_d;
     const double lnkf = ln_kf<true, GEN>(m, r, kind, lnT, invT, st.lnP, lnkinf, dlnkf_d, dlnP_d, dlnkinf_d);
-    const DT dlnkf = DT(dlnkf_d), dlnkinf = DT(dlnkinf_d);
+    const DT dlnkf = DT(dlnkf_d);
     double kf, kr;
     rate_constants<GEN>(m, A, aG, r, rev, nre, npr, lnkf, logPRT, lnT, invT, kf, kr);
     double dh = 0.0;
@@ -423,7 +423,13 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
       for (int q2 = row_lo; q2 < row_hi; q2++) {
         const RowNu rn = m.rows[q2];
         const DT v = nu_times_t<DT>(rn.nu, rn.nud, Bi);
-        for (int j = 0; j < ns - 1; j++) if (w) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
+        if (FMT == PJ_CSR) {
+          // a dense row holds every species column, contiguous in CSR
+          const int64_t e2 = jpos<FMT>(m, rn.k + 2, 2);
+          for (int j = 0; j < ns - 1; j++) if (w) jred(J, e2 + j, ld, s, v);
+        } else {
+          for (int j = 0; j < ns - 1; j++) if (w) jred(J, jpos<FMT>(m, rn.k + 2, j + 2), ld, s, v);
+        }
       }
       ATB = ATB + dE * Bi;
       ASB = ASB + dW * Bi;

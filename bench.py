@@ -35,9 +35,11 @@ METRIC = "Jacobian & source-term evals/s (states/s) at FP64 tol vs oracle; roofl
 UNIT = "states/s"
 WORKLOAD = "gri53_1m"
 
-# FP64 cost of CUDA's exp / log / divide in DFMA issue slots, measured on this
-# GB300 (dfma 505 G/s, exp 31.5 G/s, log 16.7 G/s, div 88.9 G/s).
-W_EXP, W_LOG, W_DIV = 16.0, 30.2, 5.7
+# FP64 cost of an exp / log / divide in DFMA-equivalents: the kernels' exp is
+# the table-driven one (9 FP64 operations: reduction 3, polynomial 4, table
+# product 1, shift 1); log and divide are CUDA's, measured on this GB300 in
+# DFMA issue slots (dfma 505 G/s, log 16.7 G/s, div 88.9 G/s).
+W_EXP, W_LOG, W_DIV = 9.0, 30.2, 5.7
 # FP64 peak derived from unit counts and clock: 2 DFMA / clock / SM
 # (1.25 TFLOP/s nominal for GB300) x 152 SMs x 2070 MHz.
 FP64_DFMA_PER_CLK_SM = 2.0
@@ -48,8 +50,9 @@ CPU_SAMPLE = 4096   # states of the oracle's timed sample (10-30 s of one core)
 
 def fp64_work_per_state(m, jacobian=True):
     """Algorithmic FP64 work per state in DFMA-equivalents: every add, multiply
-    and FMA of the formulas counts 1, exp 16.0, log 30.2 and divide 5.7 (the
-    measured cost of CUDA's FP64 routines on this part in DFMA issue slots).
+    and FMA of the formulas counts 1, exp 9 (the FP64 operations of the
+    table-driven exp), log 30.2 and divide 5.7 (CUDA's routines on this part,
+    in DFMA issue slots).
     The Jacobian's entry accumulations run as L2 reductions and are not
     counted."""
     import synth

@@ -194,7 +194,7 @@ def lu_work_per_state(h):
 # hash of the kernel sources at capture time; a number is only used while
 # the sources are unchanged.
 PROFILE_OF = {("jac_csr", "gri53"): "k_jacobian_tm_gri53.md", ("source", "gri53"): "k_source_terms_gri53.md",
-              ("lu", "gri53"): "k_lu_factor_gri53.md", ("ragged", "ic5874"): "k_batched_ic5874.md"}
+              ("lu", "gri53"): "k_lu_factor_gri53.md"}
 
 
 def sources_hash():

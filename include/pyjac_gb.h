@@ -269,6 +269,27 @@ int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int6
                                     const double* d_param, const double* d_phi, int64_t ld,
                                     double* d_vals, double* d_dphi, int* d_status, void* stream);
 
+/* Source terms and sparse Jacobian (the operation of pj_eval_jacobian_sparse,
+ * Sec. 2.2 and 3.4) of n states held in HOST memory, the transfers inside the
+ * call.  h_param[s] and h_phi[v*n + s] in; h_vals[e*n + s] (pattern of fmt,
+ * PJ_CSR or PJ_CSC) and h_dphi[v*n + s] out; the host arrays' leading
+ * dimension is n.  The states go through the GPU in chunks of `chunk` states
+ * (0: as many as fit 4 GiB of staging per chunk) and three device staging
+ * slots, uploads, kernels and downloads on separate streams so that the
+ * transfers of one chunk overlap the kernel of another.  Page-locked host
+ * buffers (cudaHostAlloc or cudaHostRegister) let the copies run
+ * asynchronously at full bandwidth; pageable ones work but serialise.
+ * The call orders itself after the work queued on `stream`, allocates its
+ * staging (3 slots of (2 (Ns+1) + 1 + nnz) x chunk doubles plus the
+ * Jacobian workspace) and its streams, and returns once the outputs are on
+ * the host.  h_status (host, nullable) receives the number of invalid
+ * states.  Errors: PJ_ERR_ARG, PJ_ERR_NOMEM (staging does not fit: pass a
+ * smaller chunk), PJ_ERR_UNSUPPORTED (n x 8 bytes beyond the device's copy
+ * pitch limit), PJ_ERR_CUDA. */
+int pj_eval_jacobian_sparse_host(const pj_mech* mech, int mode, int fmt, int64_t n, const double* h_param,
+                                 const double* h_phi, double* h_vals, double* h_dphi, int* h_status, int64_t chunk,
+                                 void* stream);
+
 /* operation ids for pj_workspace_size */
 #define PJ_OP_SOURCE 0
 #define PJ_OP_JACOBIAN 1

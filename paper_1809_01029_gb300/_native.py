@@ -84,6 +84,8 @@ SIGNATURES = {
     "pj_plan_launch": (C.c_int, [_vp, _vp]),
     "pj_eval_jacobian_sparse_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
                                                   _vp, _vp, _vp]),
+    "pj_eval_jacobian_sparse_host": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                               C.c_int64, _vp]),
 }
 
 _lib = None

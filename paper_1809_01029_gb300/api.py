@@ -238,6 +238,30 @@ def pj_eval_jacobian_sparse_noalloc(mech, mode, fmt, n, param, phi, ld, vals, dp
                  "pj_eval_jacobian_sparse_noalloc")
 
 
+def _hptr(a):
+    """Address of a host array: a CPU torch tensor or a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise TypeError("host buffer expected, got a CUDA tensor")
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def pj_eval_jacobian_sparse_host(mech, mode, fmt, n, h_param, h_phi, h_vals, h_dphi, chunk=0, stream=None):
+    """Source terms and sparse Jacobian of n states in host memory (leading
+    dimension n), transfers inside the call, chunked and overlapped with the
+    kernels; returns the number of invalid states.  Page-locked buffers
+    (torch pin_memory) give the overlapped, full-bandwidth path."""
+    st = C.c_int(0)
+    check(N.load().pj_eval_jacobian_sparse_host(mech.handle, mode, fmt, n, _hptr(h_param), _hptr(h_phi),
+                                                 _hptr(h_vals), _hptr(h_dphi), C.byref(st), int(chunk),
+                                                 _stream(stream)),
+          "pj_eval_jacobian_sparse_host")
+    return st.value
+
+
 # ---------------------------------------------------------------------------
 # convenience wrappers (torch tensors in, torch tensors out)
 # ---------------------------------------------------------------------------
@@ -285,6 +309,25 @@ def jacobian_sparse(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, sta
     work, wb = _workspace(mech, PJ_OP_JACOBIAN, n, phi.device)
     pj_eval_jacobian_sparse(mech, mode, fmt, n, param, phi, ld, out, dphi, status, work, wb, stream)
     return out
+
+
+def jacobian_sparse_host(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, chunk=0, pin=True):
+    """jacobian_sparse for host (CPU) float64 tensors phi [Ns+1, n] and param
+    [n], both contiguous: returns (values [nnz, n], source terms [Ns+1, n],
+    invalid-state count), the outputs in host memory (page-locked when
+    allocated here with pin=True)."""
+    import torch
+    if phi.dtype != torch.float64 or param.dtype != torch.float64 or phi.is_cuda or param.is_cuda:
+        raise TypeError("phi and param must be float64 CPU tensors")
+    if phi.dim() != 2 or phi.shape[0] != mech.n_species + 1 or not phi.is_contiguous() or not param.is_contiguous():
+        raise ValueError("phi must be a contiguous [Ns+1, n] tensor and param a contiguous [n] tensor")
+    n = phi.shape[1]
+    if out is None:
+        out = torch.empty((mech.nnz, n), dtype=torch.float64, pin_memory=pin)
+    if dphi is None:
+        dphi = torch.empty((mech.n_species + 1, n), dtype=torch.float64, pin_memory=pin)
+    bad = pj_eval_jacobian_sparse_host(mech, mode, fmt, n, param, phi, out, dphi, chunk)
+    return out, dphi, bad
 
 
 def jacobian_fd(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=None, stream=None):

@@ -124,6 +124,10 @@ def test_argument_errors(lib):
     assert f(h.handle, 0, 4, None, p, 4, p, None, None, 0, None) == N.PJ_ERR_ARG
     g = lib.pj_eval_jacobian_sparse
     assert g(h.handle, 0, 2, 1, p, p, 1, p, None, None, None, 0, None) == N.PJ_ERR_ARG  # fmt
+    hh = lib.pj_eval_jacobian_sparse_host
+    assert hh(h.handle, 0, 2, 1, p, p, p, p, None, 0, None) == N.PJ_ERR_ARG              # fmt
+    assert hh(h.handle, 0, 0, 1, p, p, p, p, None, -5, None) == N.PJ_ERR_ARG             # chunk < 0
+    assert hh(h.handle, 0, 0, 1, p, p, p, None, None, 0, None) == N.PJ_ERR_ARG           # no h_dphi
     assert lib.pj_workspace_size(h.handle, 99, 10, C.byref(C.c_size_t())) == N.PJ_ERR_ARG
     assert b"fmt" in lib.pj_last_error() or len(lib.pj_last_error()) > 0
 
@@ -139,6 +143,8 @@ def test_no_device_means_no_silent_fallback(lib):
     h = pj.pj_mech_create(tm.all_kinds())
     p = C.c_void_p(16)
     rc = lib.pj_eval_source_terms(h.handle, 0, 1, p, p, 1, p, None, None, 0, None)
+    assert rc == N.PJ_ERR_CUDA
+    rc = lib.pj_eval_jacobian_sparse_host(h.handle, 0, 0, 1, p, p, p, p, None, 0, None)
     assert rc == N.PJ_ERR_CUDA
 
 

@@ -177,3 +177,31 @@ def test_mechanism_file_gives_identical_results(pj, mechs, tmp_path):
         d_phi, d_par = to_dev(phi), to_dev(par)
         assert torch.equal(pj.source_terms(h1, mode, d_phi, d_par), pj.source_terms(h2, mode, d_phi, d_par))
         assert torch.equal(pj.jacobian_sparse(h1, mode, d_phi, d_par), pj.jacobian_sparse(h2, mode, d_phi, d_par))
+
+
+@pytest.mark.parametrize("fmt", ["csr", "csc"])
+def test_host_buffer_entry_equals_device_entry(pj, mechs, fmt):
+    """pj_eval_jacobian_sparse_host (host buffers, chunked and overlapped
+    transfers) gives the device entry's bits: several chunks with a ragged
+    last one from page-locked buffers, one chunk from pageable numpy arrays,
+    and the invalid-state count."""
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m)
+    f = pj.PJ_CSR if fmt == "csr" else pj.PJ_CSC
+    n = 5000
+    phi, par = synth.make_states(m, n, 61, synth.CONP)
+    phi[0, 4321] = -1.0                                   # one invalid state
+    ref = pj.jacobian_sparse(h, synth.CONP, to_dev(phi), to_dev(par), fmt=f).cpu().numpy()
+    ref_f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device="cuda")
+    pj.jacobian_sparse(h, synth.CONP, to_dev(phi), to_dev(par), fmt=f, dphi=ref_f)
+    ref_f = ref_f.cpu().numpy()
+    vals, dphi, bad = pj.jacobian_sparse_host(h, synth.CONP, torch.from_numpy(phi), torch.from_numpy(par), fmt=f,
+                                              chunk=1024)
+    assert bad == 1
+    assert np.array_equal(vals.numpy(), ref, equal_nan=True)
+    assert np.array_equal(dphi.numpy(), ref_f, equal_nan=True)
+    v2 = np.full((h.nnz, n), 7.0)
+    d2 = np.full((m.n_species + 1, n), 7.0)
+    assert pj.pj_eval_jacobian_sparse_host(h, synth.CONP, f, n, par, phi, v2, d2) == 1
+    assert np.array_equal(v2, ref, equal_nan=True) and np.array_equal(d2, ref_f, equal_nan=True)

@@ -812,9 +812,9 @@ def main():
         if args.op == "jac_csr":
             procs = max(1, min(os.cpu_count() or 1, 64))
             try:
-                va, dta = oracle_baseline_parallel(m, mode, 1024, 2018 + 2, procs)
+                va, dta = oracle_baseline_parallel(m, mode, CPU_SAMPLE, 2018 + 2, procs)
                 cpu_all = {"value": va, "unit": UNIT, "cores": procs, "kind": "oracle",
-                           "sample": f"{1024 * procs} states of the {m.name} mechanism on {procs} processes "
+                           "sample": f"{CPU_SAMPLE * procs} states of the {m.name} mechanism on {procs} processes "
                                      f"({dta:.1f} s)"}
             except Exception as e:  # noqa: BLE001 -- the figure is context only
                 cpu_all = {"unavailable": str(e)[:200]}

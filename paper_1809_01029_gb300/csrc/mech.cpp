@@ -231,6 +231,78 @@ int mech_build(pj_mech* m) {
   int nr_plain = 0;
   while (nr_plain < nr && !special(m->perm[nr_plain])) nr_plain++;
 
+  // Within each group of equal kind, order reactions so that those writing
+  // the same Jacobian entries run close together: the resident warps'
+  // Jacobians far exceed L2, so an entry's reductions hit L2 only while its
+  // line is recent.  Greedy: the next reaction is the one among the group's
+  // next kLook candidates sharing the most entries with the last kRecent
+  // reactions (ties: the earlier one).
+  {
+    constexpr int kLook = 256, kRecent = 6;
+    auto entries = [&](int i) {
+      std::vector<int> nu = net_nu(m, i);
+      std::vector<int> rows, cols;
+      for (int k = 0; k < bath; k++)
+        if (nu[k] != 0) rows.push_back(k);
+      for (int a = 0; a < PJ_MAX_SP; a++) {
+        const int kr = m->reac_sp[i * PJ_MAX_SP + a], kp = m->prod_sp[i * PJ_MAX_SP + a];
+        if (kr >= 0 && kr != bath) cols.push_back(kr);
+        if (m->rev[i] && kp >= 0 && kp != bath) cols.push_back(kp);
+      }
+      if (has_third_body(m->kind[i]))
+        for (int e = m->eff_ptr[i]; e < m->eff_ptr[i + 1]; e++)
+          if (m->eff_sp[e] != bath && m->eff_val[e] != 1.0) cols.push_back(m->eff_sp[e]);
+      std::vector<int64_t> ent;
+      for (int k : rows) {
+        ent.push_back((int64_t)(k + 2) * N + 0);
+        ent.push_back((int64_t)(k + 2) * N + 1);
+        for (int j : cols) ent.push_back((int64_t)(k + 2) * N + j + 2);
+      }
+      for (int j : cols) {
+        ent.push_back(j + 2);
+        ent.push_back((int64_t)N + j + 2);
+      }
+      std::sort(ent.begin(), ent.end());
+      ent.erase(std::unique(ent.begin(), ent.end()), ent.end());
+      return ent;
+    };
+    std::vector<std::vector<int64_t>> ent(nr);
+    for (int i = 0; i < nr; i++) ent[i] = entries(i);
+    auto shared = [](const std::vector<int64_t>& a, const std::vector<int64_t>& b) {
+      int c = 0;
+      size_t x = 0, y = 0;
+      while (x < a.size() && y < b.size()) {
+        if (a[x] < b[y]) x++;
+        else if (b[y] < a[x]) y++;
+        else { c++; x++; y++; }
+      }
+      return c;
+    };
+    for (int g0 = 0; g0 < nr;) {
+      int g1 = g0 + 1;
+      while (g1 < nr && special(m->perm[g1]) == special(m->perm[g0]) && m->kind[m->perm[g1]] == m->kind[m->perm[g0]])
+        g1++;
+      std::vector<int> rest(m->perm.begin() + g0, m->perm.begin() + g1), out;
+      while (!rest.empty()) {
+        size_t best = 0;
+        int best_score = -1;
+        for (size_t c = 0; c < rest.size() && c < (size_t)kLook; c++) {
+          int score = 0;
+          for (size_t q = out.size() > (size_t)kRecent ? out.size() - kRecent : 0; q < out.size(); q++)
+            score += shared(ent[rest[c]], ent[out[q]]);
+          if (score > best_score) {
+            best_score = score;
+            best = c;
+          }
+        }
+        out.push_back(rest[best]);
+        rest.erase(rest.begin() + (ptrdiff_t)best);
+      }
+      std::copy(out.begin(), out.end(), m->perm.begin() + g0);
+      g0 = g1;
+    }
+  }
+
   std::vector<double> nasa((size_t)ns * NASA_STRIDE, 0.0), wfac(ns);
   for (int k = 0; k < ns; k++) {
     for (int r = 0; r < 2; r++) {

@@ -1,6 +1,7 @@
-"""Planted mistakes: each plausible slip in the oracle's formulas must make at
-least one pin fail.  The mistake is planted in a copy of the oracle's source
-on the CPU; the real oracle is untouched."""
+"""Planted mistakes: each plausible slip in the oracle's formulas (the source
+terms and Jacobian of oracle/kinetics.py, the vector-Jacobian product of
+oracle/forms.py) must make at least one pin fail.  The mistake is planted in
+a copy of the oracle's source on the CPU; the real oracle is untouched."""
 import importlib.util
 import math
 import os
@@ -209,6 +210,112 @@ MUTATIONS = [
     ("                    cmod[i] = F / (1 + Pr)", "                    cmod[i] = F / (1 + 1 / Pr)"),
     ("        if mech.reversible[i] and mech.rev_explicit[i]:", "        if False:"),
 ]
+
+
+# ---- the vector-Jacobian product (oracle/forms.py) -------------------------
+FORMS = os.path.join(os.path.dirname(SRC), "forms.py")
+
+
+def forms_mutant(old, new):
+    """oracle.forms with one planted mistake, on the real oracle.kinetics."""
+    src = open(FORMS).read()
+    assert old in src, old
+    src = src.replace(old, new, 1).replace("from .kinetics import", "from oracle.kinetics import")
+    mod = types.ModuleType("forms_mutant")
+    exec(compile(src, "forms_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def _y_real(m, mode, phi, par):
+    """y = (wdot_0 .. wdot_{Ns-1}, dT/dt) from the real (pinned) rates and
+    source terms."""
+    import oracle.kinetics as K
+    r = K.rates(m, mode, phi, par)
+    f, _ = K.source_terms_from_rates(m, mode, r)
+    return np.concatenate([r["wdot"], f[:1]], axis=0)
+
+
+def pin_vjp_state(F, mode):
+    """g_Phi against u^T dy/dPhi built from the pinned Jacobian of f (the
+    identities of tests/test_oracle_vjp.py)."""
+    import oracle.kinetics as K
+    m = tm.all_kinds()
+    phi, par = synth.make_states(m, 2, 5, mode)
+    uw, uT = synth.make_cotangents(m.n_species, 2, 5)
+    g, _ = F.vjp(m, mode, phi, par, uw, uT)
+    J = K.jacobian(m, mode, phi, par)
+    f = K.source_terms(m, mode, phi, par)
+    V = phi[1] if mode == 0 else par
+    ns = m.n_species
+    dw = J[2:] / V
+    if mode == 0:
+        dw[:, 1] = (J[2:, 1] - f[2:] / V) / V
+    dwb = -np.einsum("k,kjn->jn", m.W[:-1] / m.W[-1], dw)
+    want = np.einsum("kn,kjn->jn", uw[: ns - 1], dw) + uw[ns - 1] * dwb + uT * J[0]
+    scale = np.einsum("kn,kjn->jn", np.abs(uw[: ns - 1]), np.abs(dw)) + np.abs(uw[ns - 1] * dwb) + np.abs(uT * J[0])
+    return bool(np.all(np.abs(g - want) <= 1e-8 * scale.max(axis=0) + 1e-300))
+
+
+def pin_vjp_theta(F, mode):
+    """g_theta of one-reaction mechanisms against central differences of
+    sum_s u . y (y from the real rates) over copies with ln A, beta or Ea
+    moved."""
+    H, O, H2, O2, OH, H2O, HO2 = range(7)
+    cases = [dict(reac=[(H, 1), (O2, 1)], prod=[(OH, 1), (O, 1)], A=2.0e11, beta=-0.3, Ea=15000.0),
+             dict(reac=[(OH, 2)], prod=[(H2, 1), (O2, 1)], A=7.0e10, beta=-0.4, Ea=1200.0, kind=synth.TROE,
+                  A0=2.0e12, beta0=-0.8, Ea0=-1500.0, troe=(0.7, 90.0, 1800.0, 5000.0), eff={H2O: 6.0})]
+    ok = True
+    for rx in cases:
+        m = tm.single(rx)
+        phi, par = synth.make_states(m, 2, 8, mode)
+        uw, uT = synth.make_cotangents(m.n_species, 2, 8)
+        _, g = F.vjp(m, mode, phi, par, uw, uT)
+        u = np.concatenate([uw, uT[None]], axis=0)
+        for p in range(3):
+            mp, mm = m.copy(), m.copy()
+            d = (1e-5, 1e-6, 1e-6 * max(abs(m.Ea[0]), 100.0))[p]
+            if p == 0:
+                mp.A[0], mm.A[0] = m.A[0] * math.exp(d), m.A[0] * math.exp(-d)
+            elif p == 1:
+                mp.beta[0], mm.beta[0] = m.beta[0] + d, m.beta[0] - d
+            else:
+                mp.Ea[0], mm.Ea[0] = m.Ea[0] + d, m.Ea[0] - d
+            dy = (_y_real(mp, mode, phi, par) - _y_real(mm, mode, phi, par)) / (2 * d)
+            ok &= bool(abs(g[0, p] - np.sum(u * dy)) <= 1e-6 * np.sum(np.abs(u * dy)))
+    return ok
+
+
+def forms_pins(F):
+    return dict(state_conp=pin_vjp_state(F, 0), state_conv=pin_vjp_state(F, 1),
+                theta_conp=pin_vjp_theta(F, 0), theta_conv=pin_vjp_theta(F, 1))
+
+
+FORMS_MUTATIONS = [
+    # sign of the dT/dt part of dy/dq
+    ("w_q = w_q - (nu.T @ E) * (u_T / aux[\"den\"])", "w_q = w_q + (nu.T @ E) * (u_T / aux[\"den\"])"),
+    # the energy-equation denominator dropped
+    ("(u_T / aux[\"den\"])[None, :]", "u_T[None, :]"),
+    # complex step in Ea not matched by its divisor
+    ("Ea=mech.Ea + 1j * hE)", "Ea=mech.Ea + 2j * hE)"),
+    # derivative with respect to A instead of ln A
+    ("A_c = mech.A * np.exp(1j * hA)", "A_c = mech.A + 1j * hA"),
+    # dV/dt (or dP/dt) in place of dT/dt as the last output
+    ("np.concatenate([r[\"wdot\"], f[:1]], axis=0)", "np.concatenate([r[\"wdot\"], f[1:2]], axis=0)"),
+    # the cotangent of the bath gas dropped from g_Phi
+    ("u = np.concatenate([u_wdot, u_T[None, :]], axis=0)        # [Ns+1, n]",
+     "u = np.concatenate([u_wdot[:-1], 0 * u_wdot[-1:], u_T[None, :]], axis=0)"),
+]
+
+
+def test_real_forms_pass_vjp_pins():
+    res = forms_pins(forms_mutant("import numpy as np", "import numpy as np"))
+    assert all(res.values()), res
+
+
+@pytest.mark.parametrize("old,new", FORMS_MUTATIONS)
+def test_planted_vjp_mistake_is_caught(old, new):
+    res = forms_pins(forms_mutant(old, new))
+    assert not all(res.values()), f"mutation {old!r} -> {new!r} escaped the VJP pins: {res}"
 
 
 def test_real_oracle_passes_compact_pins(mechs):

@@ -100,8 +100,9 @@ def nasa7(mech, T):
 # reaction rates (Sec. 2.2: R_i, c_i; modified Arrhenius; falloff forms)
 # ---------------------------------------------------------------------------
 def arrhenius(A, beta, Ea, T):
-    """Modified Arrhenius k = A T^beta exp(-Ea / (R_cal T)), Ea in cal/mol."""
-    return A * T ** beta * np.exp(-Ea / (R_CAL * T))
+    """Modified Arrhenius k = A T^beta exp(-Ea / (R_cal T)), Ea in cal/mol,
+    written in its logarithmic form exp(ln A + beta ln T - Ea / (R_cal T))."""
+    return np.exp(np.log(A) + beta * np.log(T) - Ea / (R_CAL * T))
 
 
 def net_stoich(mech):
@@ -199,9 +200,9 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_ba
     freeze_bath=True gives the rates behind the approximate Jacobian
     (Sec. 3.4, "Sparsity patterns"): the values are unchanged, but the rates
     of progress see the bath gas through Re(C_Ns) only, and the third-body
-    concentration is [M] = alpha . C_rate + (C_Ns - Re C_Ns), C_rate being C
-    with Re(C_Ns) in the bath-gas slot: a perturbation of C_Ns enters [M] with
-    unit efficiency.  Under a complex-step perturbation of a species amount
+    concentration is [M] = C_tot + sum_k (alpha_k - 1) C_rate,k, C_rate being
+    C with Re(C_Ns) in the bath-gas slot (equal to alpha . C_rate + (C_Ns -
+    Re C_Ns)): a perturbation of C_Ns enters [M] with unit efficiency.  Under a complex-step perturbation of a species amount
     n_j (C_tot real) the rates of progress then see no change of C_Ns and
     d[M]/dn_j = (alpha_j - 1)/V instead of (alpha_j - alpha_Ns)/V.
     """
@@ -240,19 +241,26 @@ def rates(mech, mode, phi, param, A=None, beta=None, Ea=None, dC=None, freeze_ba
         if mech.reversible[i] and mech.rev_explicit[i]:
             kr[i] = arrhenius(*mech.rev_arr[i], T)
         elif mech.reversible[i]:
+            # K_c = exp(-sum_k nu_k g_k/RT + (sum_k nu_k) ln(P_atm / RT)),
+            # k_r = k_f / K_c = k_f exp(-ln K_c)
             dg = sum(nu[k, i] * g[k] for k in range(ns) if nu[k, i] != 0)
             dn = float(nu[:, i].sum())
-            Kc = np.exp(-dg) * (P_ATM / (R * T)) ** dn
-            kr[i] = kf[i] / Kc
+            lnKc = -dg + dn * np.log(P_ATM / (R * T))
+            kr[i] = kf[i] * np.exp(-lnKc)
         else:
             kr[i] = 0.0
         if kind in (ELEMENTARY, PLOG, CHEB):
             cmod[i] = 1.0
         else:
-            M = third_body_alpha(mech, i) @ Cr.reshape(ns, -1)
-            M = M.reshape(np.shape(T))
-            if freeze_bath:
-                M = M + (C[ns - 1] - Cr[ns - 1])
+            # [M] = sum_k alpha_k C_k written as C_tot + sum_k (alpha_k - 1) C_k
+            # (sum_k C_k = C_tot): only non-default efficiencies enter the sum.
+            # With freeze_bath the rates see Re(C_Ns), and C_tot carries the
+            # perturbation of C_Ns with unit efficiency.
+            alpha = third_body_alpha(mech, i)
+            M = Ctot * np.ones(np.shape(T))
+            for k in range(ns):
+                if alpha[k] != 1.0:
+                    M = M + (alpha[k] - 1.0) * Cr[k]
             if kind == THIRD_BODY:
                 cmod[i] = M
             else:

@@ -185,8 +185,10 @@ def all_pins(K, mechs):
 
 
 MUTATIONS = [
-    ("np.exp(-dg) * (P_ATM", "np.exp(dg) * (P_ATM"),
-    ("(P_ATM / (R * T)) ** dn", "(P_ATM / (R * T)) ** (-dn)"),
+    ("lnKc = -dg + dn", "lnKc = dg + dn"),
+    ("+ dn * np.log(P_ATM / (R * T))", "- dn * np.log(P_ATM / (R * T))"),
+    ("kr[i] = kf[i] * np.exp(-lnKc)", "kr[i] = kf[i] * np.exp(lnKc)"),
+    ("np.exp(np.log(A) + beta * np.log(T) - Ea", "np.exp(np.log(A) + beta * np.log(T) + Ea"),
     ("a[2] * T ** 2 / 3 + a[3]", "a[2] * T ** 2 / 2 + a[3]"),
     ("s[k] = a[0] * lnT", "s[k] = a[0] * T"),
     ("+ a[5] / T", "+ a[5] * T"),
@@ -200,7 +202,8 @@ MUTATIONS = [
     ("f[1] = V * Tdot / T + (R * T * V / P) * Om", "f[1] = V * Tdot / T + (R * V / P) * Om"),
     ("f[1] = P * Tdot / T + R * T * Om", "f[1] = P * Tdot / T + R * Om"),
     # approximate Jacobian (Sec. 3.4)
-    ("                M = M + (C[ns - 1] - Cr[ns - 1])", "                M = M"),
+    ("M = M + (alpha[k] - 1.0) * Cr[k]", "M = M + (alpha[k] - 1.0) * C[k]"),
+    ("M = M + (alpha[k] - 1.0) * Cr[k]", "M = M + alpha[k] * Cr[k]"),
     ("        Cr[-1] = _re(C[-1])", "        Cr = _re(C)"),
     ("ref = 1.0 if form == APPROX else a[bath]", "ref = a[bath]"),
     ("    if dense and form != APPROX:", "    if dense:"),

@@ -348,7 +348,36 @@ def _cs_step(x):
 EXACT, APPROX = "exact", "approx"
 
 
-def jacobian(mech, mode, phi, param, with_parts=False, form=EXACT):
+def _cs_columns(task):
+    """Complex-step derivatives of f, of the forward / reverse parts and of
+    the energy-equation denominator for the state columns `cols` (one task of
+    jacobian's map), in the complex type matching phi's precision."""
+    mech, mode, phi, param, cols, form = task
+    ctype = np.clongdouble if phi.dtype == np.longdouble else np.complex128
+    out = []
+    for j in cols:
+        ph = phi.astype(ctype)
+        hj = _cs_step(phi[j])
+        ph[j] = ph[j] + 1j * hj
+        r = rates(mech, mode, ph, param.astype(ctype), freeze_bath=(form == APPROX and j >= 2))
+        f, aux = source_terms_from_rates(mech, mode, r)
+        out.append((f.imag / hj, r["qf"].imag / hj, r["qr"].imag / hj, aux["den"].imag / hj))
+    return out
+
+
+def _chunks(items, k):
+    """items split into at most k contiguous, nearly equal runs."""
+    k = max(1, min(k, len(items)))
+    q, r = divmod(len(items), k)
+    out, lo = [], 0
+    for c in range(k):
+        hi = lo + q + (c < r)
+        out.append(items[lo:hi])
+        lo = hi
+    return out
+
+
+def jacobian(mech, mode, phi, param, with_parts=False, form=EXACT, map_fn=map, chunks=1):
     """Dense Jacobian [Ns+1, Ns+1, n] of f with P (CONP) or V (CONV) fixed.
 
     Column j is Im f(Phi + i h e_j) / h with h = 1e-30 max(|Phi_j|, 1):
@@ -366,25 +395,28 @@ def jacobian(mech, mode, phi, param, with_parts=False, form=EXACT):
     efficiency spreads over every species, are left out (rates(freeze_bath=
     True)).  The T and S columns, and every other use of C_Ns (the heat
     capacity of the mixture), stay exact.
+
+    The columns are independent: map_fn (a parallel map, e.g. a process
+    pool's) may evaluate them in `chunks` groups; the result is the same.
+    With phi and param in np.longdouble the whole evaluation runs in that
+    type (the extended-precision reference of the FP64 oracle).
     """
     if form not in (EXACT, APPROX):
         raise ValueError(f"unknown Jacobian form {form!r}")
     N = mech.n_species + 1
     n = phi.shape[1]
-    J = np.empty((N, N, n))
-    parts = dict(dqf=np.empty((mech.n_reactions, N, n)), dqr=np.empty((mech.n_reactions, N, n)),
-                 dden=np.empty((N, n)))
-    for j in range(N):
-        ph = phi.astype(np.complex128)
-        hj = _cs_step(phi[j])
-        ph[j] = ph[j] + 1j * hj
-        r = rates(mech, mode, ph, param.astype(np.complex128), freeze_bath=(form == APPROX and j >= 2))
-        f, aux = source_terms_from_rates(mech, mode, r)
-        J[:, j] = f.imag / hj
-        if with_parts:
-            parts["dqf"][:, j] = r["qf"].imag / hj
-            parts["dqr"][:, j] = r["qr"].imag / hj
-            parts["dden"][j] = aux["den"].imag / hj
+    rt = np.longdouble if phi.dtype == np.longdouble else np.float64
+    J = np.empty((N, N, n), dtype=rt)
+    parts = dict(dqf=np.empty((mech.n_reactions, N, n), dtype=rt), dqr=np.empty((mech.n_reactions, N, n), dtype=rt),
+                 dden=np.empty((N, n), dtype=rt))
+    groups = _chunks(list(range(N)), chunks)
+    for cols, res in zip(groups, map_fn(_cs_columns, [(mech, mode, phi, param, c, form) for c in groups])):
+        for j, (df, dqf, dqr, dden) in zip(cols, res):
+            J[:, j] = df
+            if with_parts:
+                parts["dqf"][:, j] = dqf
+                parts["dqr"][:, j] = dqr
+                parts["dden"][j] = dden
     if with_parts:
         return J, parts
     return J
@@ -437,8 +469,26 @@ def source_term_envelope(mech, mode, phi, param):
     return f, np.maximum(env, np.abs(f))
 
 
-def jacobian_envelope(mech, mode, phi, param):
-    """Jacobian J [N, N, n] and an absolute envelope of equal shape.
+def _dC_columns(task):
+    """|dq'/dC_k| + |dq''/dC_k| per reaction for the species `species`, by
+    complex step in C_k alone (one task of jacobian_envelope's map)."""
+    mech, mode, phi, param, species = task
+    ns = mech.n_species
+    shape = (phi.shape[1],)
+    _, _, _, C, _ = concentrations(mech, mode, phi, param)
+    out = []
+    for k in species:
+        hk = 1e-30 * np.maximum(np.abs(C[k]), 1e-200)
+        dC = np.zeros((ns,) + shape, dtype=np.complex128)
+        dC[k] = 1j * hk
+        rk = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128), dC=dC)
+        out.append((np.abs(rk["qf"].imag) + np.abs(rk["qr"].imag)) / hk)
+    return out
+
+
+def jacobian_envelope(mech, mode, phi, param, map_fn=map, chunks=1):
+    """Jacobian J [N, N, n] and an absolute envelope of equal shape (map_fn,
+    chunks: as for jacobian).
 
     Per reaction, the envelope of d q_i / d Phi_j sums the magnitudes of the
     forward and reverse parts and of the paths through the bath-gas
@@ -449,7 +499,7 @@ def jacobian_envelope(mech, mode, phi, param):
     Species rows combine these with |nu_ki|; energy / state rows follow the
     structure of the source terms.
     """
-    J, parts = jacobian(mech, mode, phi, param, with_parts=True)
+    J, parts = jacobian(mech, mode, phi, param, with_parts=True, map_fn=map_fn, chunks=chunks)
     r = rates(mech, mode, phi, param)
     f, aux = source_terms_from_rates(mech, mode, r)
     _, envf = source_term_envelope(mech, mode, phi, param)
@@ -459,12 +509,10 @@ def jacobian_envelope(mech, mode, phi, param):
     shape = np.shape(T)
     # complex-step derivatives of the forward / reverse parts w.r.t. each C_k
     dC_mag = np.empty((nr, ns) + shape)
-    for k in range(ns):
-        hk = 1e-30 * np.maximum(np.abs(C[k]), 1e-200)
-        dC = np.zeros((ns,) + shape, dtype=np.complex128)
-        dC[k] = 1j * hk
-        rk = rates(mech, mode, phi.astype(np.complex128), param.astype(np.complex128), dC=dC)
-        dC_mag[:, k] = (np.abs(rk["qf"].imag) + np.abs(rk["qr"].imag)) / hk
+    groups = _chunks(list(range(ns)), chunks)
+    for ks, res in zip(groups, map_fn(_dC_columns, [(mech, mode, phi, param, g) for g in groups])):
+        for k, mag in zip(ks, res):
+            dC_mag[:, k] = mag
     bath = dC_mag[:, ns - 1]                                   # [Nr, n]
     eq = np.empty((nr, N) + shape)                             # per-reaction envelope of dq_i/dPhi_j
     eq[:, 0] = np.abs(parts["dqf"][:, 0]) + np.abs(parts["dqr"][:, 0]) + bath * Ctot / T

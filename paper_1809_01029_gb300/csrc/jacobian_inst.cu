@@ -2,14 +2,14 @@
 // build compiles this file once per pair, with
 //   PJ_INST_TM   -1: k_jacobian (arrays in shared memory or a workspace);
 //                0, 1, 2: k_jacobian_tm with that many of C_k, g_k/RT in
-//                shared memory;
+//                shared memory; 3: k_jacobian_coop (32-state tiles);
 //   PJ_INST_F32  0: FP64 Jacobian; 1: FP32 Newton matrix M = I - h gamma J;
 //   PJ_INST_NAME the launcher this unit defines (declared in launch.h),
 // so that the instantiations compile in parallel.
 #include "jacobian_kernels.cuh"
 
 #if !defined(PJ_INST_TM) || !defined(PJ_INST_F32) || !defined(PJ_INST_NAME)
-#error "compile with -DPJ_INST_TM=<-1|0|1|2> -DPJ_INST_F32=<0|1> -DPJ_INST_NAME=<launcher>"
+#error "compile with -DPJ_INST_TM=<-1|0|1|2|3> -DPJ_INST_F32=<0|1> -DPJ_INST_NAME=<launcher>"
 #endif
 
 namespace pj {
@@ -22,7 +22,14 @@ using InstDT = double;
 constexpr bool kInstNewton = false;
 #endif
 
-#if PJ_INST_TM < 0
+#if PJ_INST_TM == 3
+using InstPlan = CoopPlan;
+template <int MODE, int FMT>
+static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double*, cudaStream_t st) {
+  if (m.nr_plain < m.nr) return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, true>(m, p, n, a, st);
+  return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, false>(m, p, n, a, st);
+}
+#elif PJ_INST_TM < 0
 using InstPlan = LaunchPlan;
 template <int MODE, int FMT>
 static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double* ws,

@@ -27,7 +27,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
+#include "jacobian_kernels.cuh"  // k_jacobian_coop's tile and shared-memory size (the kernels: jacobian_inst.cu)
 #include "kinetics_state.cuh"
 #ifndef PJ_NO_LAUNCHERS
 #include "launch.h"
@@ -193,6 +196,61 @@ TmPlan tm_plan(int ns) {
   return t;
 }
 
+// Which Jacobian layout runs, chosen by measurement on GB300 (CSR, FP64
+// and FP32, mechanisms of 13 to 111 species, 4 ki to 1 Mi states):
+//  * batches smaller than one round of the one-state-per-thread kernels
+//    (SMs x 512 threads): the cooperative kernel, whose 32-state tiles spread
+//    over every SM (13 species, 4096 states: 64 M against 13 M states/s);
+//  * mechanisms whose one-state-per-thread arrays go to a global workspace
+//    (no TMEM or shared-memory layout, e.g. 111 species): cooperative, 16
+//    warps (+10 % FP64, +16 % FP32 Newton form);
+//  * the FP32 Newton form where the TMEM layout applies (53 species):
+//    cooperative, 8 warps in two blocks per SM (+6 %);
+//  * otherwise the one-state-per-thread layouts (TMEM at 53 species, 2 %
+//    ahead of the best cooperative shape; shared memory at 13 species).
+// The cooperative kernel keeps far fewer Jacobians live in L2 (32 states per
+// block, one block per SM at 16 warps: 44 KB of DRAM traffic per state at 53
+// species against 154 KB), so it is the layout to force where the Jacobian
+// shares the GPU with other memory-heavy work.
+// PYJAC_GB_JAC_LAYOUT=coop|percore forces one family (coop only where its
+// shared memory fits); PYJAC_GB_COOP_WARPS sets the warps per block (4, 8
+// or 16) and PYJAC_GB_COOP_CTAS the blocks per SM (at most 16 / warps); 8
+// warps in one block per SM run the instance compiled for 255 registers.
+static int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+
+static bool coop_shape(const DevMech& m, int warps, int ctas, CoopPlan& c) {
+  c = CoopPlan{false, warps, ctas, coop_smem_bytes(m.ns, warps), sm_count() * ctas, warps == 8 && ctas == 1};
+  if (warps != 4 && warps != 8 && warps != 16) return false;
+  if (ctas < 1 || ctas * warps > 16) return false;
+  if (c.smem + kBlockOverhead > kSmemPerSm / (size_t)ctas || c.smem > kSmemCap) return false;
+  c.use = true;
+  return true;
+}
+
+CoopPlan coop_plan(const DevMech& m, int fmt, int dt_bytes, int64_t n) {
+  (void)fmt;
+  CoopPlan c{false, 16, 1, 0, 0, false};
+  const char* lay = getenv("PYJAC_GB_JAC_LAYOUT");
+  if (lay && strcmp(lay, "percore") == 0) return c;
+  if (lay && strcmp(lay, "coop") == 0) {
+    const int warps = env_int("PYJAC_GB_COOP_WARPS", 16);
+    coop_shape(m, warps, env_int("PYJAC_GB_COOP_CTAS", 16 / std::max(warps, 1)), c);
+    return c;
+  }
+  const TmPlan t = tm_plan(m.ns);
+  const bool percore_global = !t.use && plan_for(jacobian_arrays(), m.ns, n).global_ws;
+  if (n < (int64_t)sm_count() * 512 || percore_global) {
+    coop_shape(m, 16, 1, c);
+    return c;
+  }
+  if (t.use && dt_bytes == 4 && coop_shape(m, 8, 2, c)) return c;
+  c.use = false;
+  return c;
+}
+
 size_t workspace_bytes(int arrays, int ns, int64_t n) {
   if (arrays == jacobian_arrays()) {
     const TmPlan t = tm_plan(ns);
@@ -205,6 +263,8 @@ size_t workspace_bytes(int arrays, int ns, int64_t n) {
 // check the workspace, call the launcher of that layout and precision.
 static int launch_jac_any(const DevMech& m, int mode, int fmt, int64_t n, const JacArgs& a, bool f32, void* work,
                           size_t work_bytes, cudaStream_t st) {
+  const CoopPlan c = coop_plan(m, fmt, f32 ? 4 : 8, n);
+  if (c.use) return (f32 ? launch_jac_coop_f32 : launch_jac_coop_f64)(m, c, mode, fmt, n, a, nullptr, st);
   const TmPlan t = tm_plan(m.ns);
   if (t.use) {
     if (t.ws_bytes && (!work || work_bytes < t.ws_bytes))
@@ -219,6 +279,11 @@ static int launch_jac_any(const DevMech& m, int mode, int fmt, int64_t n, const 
     return fail(PJ_ERR_NOMEM, "workspace too small for the Jacobian kernel (see pj_workspace_size)");
   double* ws = p.global_ws ? static_cast<double*>(work) : nullptr;
   return (f32 ? launch_jac_plain_f32 : launch_jac_plain_f64)(m, p, mode, fmt, n, a, ws, st);
+}
+
+int jacobian_layout(const DevMech& m, int fmt, bool f32, int64_t n) {
+  if (coop_plan(m, fmt, f32 ? 4 : 8, n).use) return PJ_LAYOUT_COOP;
+  return tm_plan(m.ns).use ? PJ_LAYOUT_TMEM : PJ_LAYOUT_PERCORE;
 }
 
 int launch_jacobian(const DevMech& m, int mode, int fmt, int64_t n, const double* param, const double* phi,

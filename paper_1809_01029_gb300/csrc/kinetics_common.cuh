@@ -342,8 +342,12 @@ template <class SA>
 __device__ __forceinline__ double third_body(const DevMech& m, const SA& A, int aC, const Rxn* __restrict__ r,
                                              double Ctot) {
   double M = Ctot;
-  for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++)
+  for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++) {
+    if (!PJ_DBG_OK(m.dbg, e >= 0 && e < m.n_eff && __ldg(m.eff_sp + e) >= 0 && __ldg(m.eff_sp + e) < m.ns,
+                   PJ_DBG_EFF))
+      break;
     M = fma(__ldg(m.eff_am1 + e), A.at(aC, __ldg(m.eff_sp + e)), M);
+  }
   return M;
 }
 

@@ -7,6 +7,25 @@
 
 namespace pj {
 
+// Bounds-checked build (compiled with -DPJ_DEBUG_BOUNDS): every lookup in an
+// index table derived at mechanism load -- the per-reaction target lists,
+// the full -> sparse position maps, the species-row and efficiency lists,
+// the LU scatter / gather maps -- is checked before use.  A bad index sets a
+// bit of the mechanism's device error word (pj_debug_word) and is replaced
+// by a harmless one (the access is skipped), so a corrupted table shows as a
+// nonzero word, never as an out-of-range access or a trap.  Without the
+// macro the checks compile to nothing.
+enum : uint32_t { PJ_DBG_TARGET = 1, PJ_DBG_POSMAP = 2, PJ_DBG_ROWS = 4, PJ_DBG_EFF = 8, PJ_DBG_LU = 16 };
+#ifdef PJ_DEBUG_BOUNDS
+__device__ __forceinline__ bool pj_dbg_ok(uint32_t* word, bool ok, uint32_t bit) {
+  if (!ok && word) atomicOr(word, bit);
+  return ok;
+}
+#define PJ_DBG_OK(word, cond, bit) pj_dbg_ok((word), (cond), (bit))
+#else
+#define PJ_DBG_OK(word, cond, bit) true
+#endif
+
 // Per-state working arrays: element (a, k) of the calling thread's state sits
 // at base[(a*ns + k) * stride].  base/stride point either into shared memory
 // (stride = blockDim.x) or into a global workspace (stride = total threads).

@@ -37,6 +37,18 @@ struct TmPlan {
   int grid;         // 0: one block per 128 states; else the persistent grid
 };
 
+// Cooperative Jacobian layout (k_jacobian_coop): `warps` warps per block
+// share a tile of 32 states, `ctas` blocks per SM, a persistent grid of
+// `grid` blocks walking the tiles.
+struct CoopPlan {
+  bool use;
+  int warps;
+  int ctas;
+  size_t smem;
+  int grid;
+  bool wide_regs;   // 8 warps, one block per SM, up to 255 registers a thread
+};
+
 constexpr size_t kSmemPerSm = 228 * 1024;                    // shared memory per SM
 constexpr size_t kSmemCap = 225 * 1024;                      // per block, less the 2 KB exp table
 constexpr size_t kBlockOverhead = 1024 + 2048 + 64;          // driver reserve, exp table, TMEM base
@@ -50,6 +62,8 @@ int source_arrays();
 int jacobian_arrays();
 LaunchPlan plan_for(int arrays, int ns, int64_t n);
 TmPlan tm_plan(int ns);
+CoopPlan coop_plan(const DevMech& m, int fmt, int dt_bytes, int64_t n);
+int jacobian_layout(const DevMech& m, int fmt, bool f32, int64_t n);   // PJ_LAYOUT_*
 size_t workspace_bytes(int arrays, int ns, int64_t n);
 size_t form_workspace_bytes(int op, const DevMech& m, int64_t n);
 
@@ -114,6 +128,10 @@ int launch_jac_tm1_f32(const DevMech& m, const TmPlan& p, int mode, int fmt, int
                        double* ws, cudaStream_t st);
 int launch_jac_tm2_f32(const DevMech& m, const TmPlan& p, int mode, int fmt, int64_t n, const JacArgs& a,
                        double* ws, cudaStream_t st);
+int launch_jac_coop_f64(const DevMech& m, const CoopPlan& p, int mode, int fmt, int64_t n, const JacArgs& a,
+                        double* ws, cudaStream_t st);
+int launch_jac_coop_f32(const DevMech& m, const CoopPlan& p, int mode, int fmt, int64_t n, const JacArgs& a,
+                        double* ws, cudaStream_t st);
 
 // Raise a kernel's dynamic shared-memory limit when it asks for more than
 // the default 48 KB.

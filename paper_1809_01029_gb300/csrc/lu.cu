@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "kinetics_device.cuh"
 #include "launch.h"
 #include "pj_internal.h"
 
@@ -120,8 +121,8 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
                                                    const double* __restrict__ hstep, double gamma,
                                                    T* __restrict__ lu, int* status, T* gws) {
   extern __shared__ __align__(16) unsigned char lu_smem[];
-  const int N = L.N, tid = threadIdx.x, nt = blockDim.x;
-  const int NN = N * N;
+  const int N = L.N, NP = L.NP, tid = threadIdx.x, nt = blockDim.x;
+  const int NN = N * NP;
   T* A = gws ? gws + (int64_t)blockIdx.x * NN : reinterpret_cast<T*>(lu_smem);
   __shared__ int bad;
   __shared__ T s_inv;
@@ -132,11 +133,13 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
     const T hg = FROM_J ? T(-hstep[s] * gamma) : T(0);
     for (int e = tid; e < L.nnz; e += nt) {
       const T v = vals[(int64_t)e * ld + s];
-      A[__ldg(L.m2d + e)] = FROM_J ? hg * v : v;
+      const int pos = __ldg(L.m2d + e);
+      if (!PJ_DBG_OK(L.dbg, pos >= 0 && pos < NN, PJ_DBG_LU)) continue;
+      A[pos] = FROM_J ? hg * v : v;
     }
     __syncthreads();
     if (FROM_J)
-      for (int k = tid; k < N; k += nt) A[k * N + k] += T(1);
+      for (int k = tid; k < N; k += nt) A[k * NP + k] += T(1);
     __syncthreads();
     // one thread forms each pivot's reciprocal ahead of its step (the FP64
     // pipe charges whole warps, so a division in every thread would cost as
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
       const int c0 = __ldg(L.cptr + k), nc = __ldg(L.cptr + k + 1) - c0;
       for (int a = tid; a < nr; a += nt) {
         const int i = __ldg(L.ridx + r0 + a);
-        A[i * N + k] *= inv;
+        A[i * NP + k] *= inv;
       }
       __syncthreads();
       // the nr x nc update.  FP64: flattened over every thread so that warps
@@ -167,21 +170,21 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
         const int a0 = nc >= nt ? 0 : tid / nc;
         for (int cj = nc >= nt ? tid : tid % nc; cj < nc && a0 < per; cj += nc >= nt ? nt : nc) {
           const int j = __ldg(L.cidx + c0 + cj);
-          const T u = A[k * N + j];
+          const T u = A[k * NP + j];
           int a = a0;
           for (; a + 3 * per < nr; a += 4 * per) {
             const int i0 = __ldg(L.ridx + r0 + a), i1 = __ldg(L.ridx + r0 + a + per);
             const int i2 = __ldg(L.ridx + r0 + a + 2 * per), i3 = __ldg(L.ridx + r0 + a + 3 * per);
-            const T l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
-            const T v0 = A[i0 * N + j], v1 = A[i1 * N + j], v2 = A[i2 * N + j], v3 = A[i3 * N + j];
-            A[i0 * N + j] = fma_t(-l0, u, v0);
-            A[i1 * N + j] = fma_t(-l1, u, v1);
-            A[i2 * N + j] = fma_t(-l2, u, v2);
-            A[i3 * N + j] = fma_t(-l3, u, v3);
+            const T l0 = A[i0 * NP + k], l1 = A[i1 * NP + k], l2 = A[i2 * NP + k], l3 = A[i3 * NP + k];
+            const T v0 = A[i0 * NP + j], v1 = A[i1 * NP + j], v2 = A[i2 * NP + j], v3 = A[i3 * NP + j];
+            A[i0 * NP + j] = fma_t(-l0, u, v0);
+            A[i1 * NP + j] = fma_t(-l1, u, v1);
+            A[i2 * NP + j] = fma_t(-l2, u, v2);
+            A[i3 * NP + j] = fma_t(-l3, u, v3);
           }
           for (; a < nr; a += per) {
             const int i = __ldg(L.ridx + r0 + a);
-            A[i * N + j] = fma_t(-A[i * N + k], u, A[i * N + j]);
+            A[i * NP + j] = fma_t(-A[i * NP + k], u, A[i * NP + j]);
           }
           if (nc < nt) break;  // one column per thread in that case
         }
@@ -206,25 +209,25 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
           step();
           const int i3 = __ldg(L.ridx + r0 + ia), j3 = __ldg(L.cidx + c0 + jc);
           step();
-          const T l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
-          const T u0 = A[k * N + j0], u1 = A[k * N + j1], u2 = A[k * N + j2], u3 = A[k * N + j3];
-          const T v0 = A[i0 * N + j0], v1 = A[i1 * N + j1], v2 = A[i2 * N + j2], v3 = A[i3 * N + j3];
-          A[i0 * N + j0] = fma_t(-l0, u0, v0);
-          A[i1 * N + j1] = fma_t(-l1, u1, v1);
-          A[i2 * N + j2] = fma_t(-l2, u2, v2);
-          A[i3 * N + j3] = fma_t(-l3, u3, v3);
+          const T l0 = A[i0 * NP + k], l1 = A[i1 * NP + k], l2 = A[i2 * NP + k], l3 = A[i3 * NP + k];
+          const T u0 = A[k * NP + j0], u1 = A[k * NP + j1], u2 = A[k * NP + j2], u3 = A[k * NP + j3];
+          const T v0 = A[i0 * NP + j0], v1 = A[i1 * NP + j1], v2 = A[i2 * NP + j2], v3 = A[i3 * NP + j3];
+          A[i0 * NP + j0] = fma_t(-l0, u0, v0);
+          A[i1 * NP + j1] = fma_t(-l1, u1, v1);
+          A[i2 * NP + j2] = fma_t(-l2, u2, v2);
+          A[i3 * NP + j3] = fma_t(-l3, u3, v3);
         }
         for (; p < tot; p += nt) {
           const int i = __ldg(L.ridx + r0 + ia), j = __ldg(L.cidx + c0 + jc);
-          A[i * N + j] = fma_t(-A[i * N + k], A[k * N + j], A[i * N + j]);
+          A[i * NP + j] = fma_t(-A[i * NP + k], A[k * NP + j], A[i * NP + j]);
           step();
         }
       }
       __syncthreads();
       if (tid == 0) {
-        A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
+        A[k * NP + k] = inv;  // the diagonal slot stores 1 / U_kk
         if (k + 1 < N) {
-          const T piv = A[(k + 1) * N + k + 1];
+          const T piv = A[(k + 1) * NP + k + 1];
           if (bad_pivot(piv)) bad = 1;
           s_inv = T(1) / piv;
         }
@@ -232,7 +235,9 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
       __syncthreads();
     }
     for (int e = tid; e < L.lu_nnz; e += nt) {
-      const T v = A[__ldg(L.l2d + e)];
+      const int pos = __ldg(L.l2d + e);
+      if (!PJ_DBG_OK(L.dbg, pos >= 0 && pos < NN, PJ_DBG_LU)) continue;
+      const T v = A[pos];
       if (nonfinite_bits(v)) bad = 1;  // overflow anywhere (FP32 range) marks the state
       lu[(int64_t)e * ld + s] = v;
     }
@@ -243,13 +248,18 @@ __global__ void __launch_bounds__(256) k_lu_factor(DevLu L, int64_t n, const T* 
 }
 
 // S states per block, the dense matrices interleaved in shared memory:
-// A[p] holds entry p (pivot-order dense position) of the block's S states.
-// The elimination is that of k_lu_factor, value for value, for each state; a
-// group's padding states (n not a multiple of S) factor the identity and are
-// neither written nor counted.  Two barriers per pivot: the reciprocal of the
-// next pivot is formed by thread 0 during the update (the next pivot's entry
-// is final once pair 0 of the update, the only one that can change it, is
-// done), overlapping the other threads' updates.
+// A[p] holds entry p (pivot-order dense position, row stride NP) of the
+// block's S states.  The elimination is that of k_lu_factor, value for value,
+// for each state; a group's padding states (n not a multiple of S) factor
+// the identity and are neither written nor counted.
+//
+// One barrier per pivot: when pivot k's update starts, column k already
+// holds its multipliers L_ik = A_ik / U_kk and A_kk holds 1 / U_kk.  Warp 0
+// takes column k+1 (the only column the next pivot scales): it applies pivot
+// k's update to it, forms 1 / U_(k+1)(k+1), and scales the column -- the fill
+// pattern is closed under elimination, so rows(k+1) holds every row of
+// rows(k) but k+1 and no entry of the column changes after pivot k -- while
+// the other warps update the pairs of every other column.
 template <typename T, int S, bool FROM_J>
 __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T* __restrict__ vals, int64_t ld,
                                                      const double* __restrict__ hstep, double gamma,
@@ -257,12 +267,33 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
   using V = typename LuVec<T, S>::V;
   extern __shared__ __align__(16) unsigned char lu_smem[];
   V* A = reinterpret_cast<V*>(lu_smem);
-  const int N = L.N, tid = threadIdx.x, nt = blockDim.x;
-  const int NN = N * N;
+  const int N = L.N, NP = L.NP, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+  const int NN = N * NP;
   __shared__ int bad[S];
   __shared__ V s_inv;
   __shared__ T s_hg[S];
   auto at = [&](int p, int q) -> T& { return reinterpret_cast<T*>(A + p)[q]; };
+  // warp 0: 1 / pivot c (all S states), stored in the diagonal slot and
+  // broadcast; then column c's entries below the pivot scaled by it
+  auto finish_column = [&](int c) {
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < S; q++) {
+        const T piv = at(c * NP + c, q);
+        if (bad_pivot(piv)) bad[q] = 1;
+        reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
+      }
+      A[c * NP + c] = s_inv;
+    }
+    __syncwarp();
+    const V inv = s_inv;
+    const int r0 = __ldg(L.rptr + c), nr = __ldg(L.rptr + c + 1) - r0;
+    for (int a = lane; a < nr; a += 32) {
+      const int i = __ldg(L.ridx + r0 + a);
+      A[i * NP + c] = v_mul(A[i * NP + c], inv);
+    }
+  };
   const int64_t groups = (n + S - 1) / S;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
     const int64_t s0 = g * S;
@@ -276,97 +307,84 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
     // consecutive threads take the S states of one entry (adjacent in vals)
     for (int t = tid; t < L.nnz * S; t += nt) {
       const int e = t / S, q = t - e * S;
-      if (q < live) {
+      const int pos = __ldg(L.m2d + e);
+      if (q < live && PJ_DBG_OK(L.dbg, pos >= 0 && pos < NN, PJ_DBG_LU)) {
         const T v = vals[(int64_t)e * ld + s0 + q];
-        at(__ldg(L.m2d + e), q) = FROM_J ? s_hg[q] * v : v;
+        at(pos, q) = FROM_J ? s_hg[q] * v : v;
       }
     }
     __syncthreads();
     for (int t = tid; t < N * S; t += nt) {
       const int k = t / S, q = t - k * S;
-      if (FROM_J || q >= live) at(k * N + k, q) += T(1);
+      if (FROM_J || q >= live) at(k * NP + k, q) += T(1);
     }
     __syncthreads();
-    if (tid == 0) {
-#pragma unroll
-      for (int q = 0; q < S; q++) {
-        const T piv = at(0, q);
-        if (bad_pivot(piv)) bad[q] = 1;
-        reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
-      }
-    }
+    if (warp == 0) finish_column(0);
     __syncthreads();
-    for (int k = 0; k < N; k++) {
-      const V inv = s_inv;
+    for (int k = 0; k < N - 1; k++) {
       const int r0 = __ldg(L.rptr + k), nr = __ldg(L.rptr + k + 1) - r0;
       const int c0 = __ldg(L.cptr + k), nc = __ldg(L.cptr + k + 1) - c0;
-      for (int a = tid; a < nr; a += nt) {
-        const int i = __ldg(L.ridx + r0 + a);
-        A[i * N + k] = v_mul(A[i * N + k], inv);
-      }
-      __syncthreads();
-      // the nr x nc update flattened over the block: pair p = a * nc + c,
-      // stride nt, four pairs at a time (distinct pairs touch distinct
-      // entries, so their loads go out first)
-      const int tot = nr * nc;
-      int p = tid;
-      if (tid == 0) {
-        A[k * N + k] = inv;  // the diagonal slot stores 1 / U_kk
-        if (k + 1 < N) {
-          // rows and columns ascend, so entry (k+1, k+1) can only be pair 0
-          const int d = (k + 1) * N + k + 1;
-          if (tot > 0 && __ldg(L.ridx + r0) == k + 1 && __ldg(L.cidx + c0) == k + 1) {
-            A[d] = v_fms(A[d - 1], A[k * N + k + 1], A[d]);
-            p = nt;
+      // column k+1 is cols(k)[0] when pivot k changes it (columns ascend)
+      const int j0 = nc > 0 && __ldg(L.cidx + c0) == k + 1 ? 1 : 0;
+      if (warp == 0) {
+        if (j0) {
+          const V u = A[k * NP + k + 1];
+          for (int a = lane; a < nr; a += 32) {
+            const int i = __ldg(L.ridx + r0 + a);
+            A[i * NP + k + 1] = v_fms(A[i * NP + k], u, A[i * NP + k + 1]);
           }
-#pragma unroll
-          for (int q = 0; q < S; q++) {
-            const T piv = at(d, q);
-            if (bad_pivot(piv)) bad[q] = 1;
-            reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
-          }
+          __syncwarp();
         }
-      }
-      if (p < tot) {
-        const int di = nt / nc, dj = nt - di * nc;
-        int ia = p / nc, jc = p - ia * nc;
-        auto step = [&]() {
-          ia += di;
-          jc += dj;
-          if (jc >= nc) {
-            jc -= nc;
-            ia++;
+        finish_column(k + 1);
+      } else {
+        // the nr x (nc - j0) update of the other columns, flattened over the
+        // other warps: pair p = a * ncw + c, four pairs at a time (distinct
+        // pairs touch distinct entries, so their loads go out first)
+        const int ncw = nc - j0, tot = nr * ncw, ntw = nt - 32;
+        int p = tid - 32;
+        if (p < tot) {
+          const int di = ntw / ncw, dj = ntw - di * ncw;
+          int ia = p / ncw, jc = p - ia * ncw;
+          auto step = [&]() {
+            ia += di;
+            jc += dj;
+            if (jc >= ncw) {
+              jc -= ncw;
+              ia++;
+            }
+          };
+          const int* __restrict__ ci = L.cidx + c0 + j0;
+          for (; p + 3 * ntw < tot; p += 4 * ntw) {
+            const int i0 = __ldg(L.ridx + r0 + ia), jj0 = __ldg(ci + jc);
+            step();
+            const int i1 = __ldg(L.ridx + r0 + ia), jj1 = __ldg(ci + jc);
+            step();
+            const int i2 = __ldg(L.ridx + r0 + ia), jj2 = __ldg(ci + jc);
+            step();
+            const int i3 = __ldg(L.ridx + r0 + ia), jj3 = __ldg(ci + jc);
+            step();
+            const V l0 = A[i0 * NP + k], l1 = A[i1 * NP + k], l2 = A[i2 * NP + k], l3 = A[i3 * NP + k];
+            const V u0 = A[k * NP + jj0], u1 = A[k * NP + jj1], u2 = A[k * NP + jj2], u3 = A[k * NP + jj3];
+            const V v0 = A[i0 * NP + jj0], v1 = A[i1 * NP + jj1], v2 = A[i2 * NP + jj2], v3 = A[i3 * NP + jj3];
+            A[i0 * NP + jj0] = v_fms(l0, u0, v0);
+            A[i1 * NP + jj1] = v_fms(l1, u1, v1);
+            A[i2 * NP + jj2] = v_fms(l2, u2, v2);
+            A[i3 * NP + jj3] = v_fms(l3, u3, v3);
           }
-        };
-        for (; p + 3 * nt < tot; p += 4 * nt) {
-          const int i0 = __ldg(L.ridx + r0 + ia), j0 = __ldg(L.cidx + c0 + jc);
-          step();
-          const int i1 = __ldg(L.ridx + r0 + ia), j1 = __ldg(L.cidx + c0 + jc);
-          step();
-          const int i2 = __ldg(L.ridx + r0 + ia), j2 = __ldg(L.cidx + c0 + jc);
-          step();
-          const int i3 = __ldg(L.ridx + r0 + ia), j3 = __ldg(L.cidx + c0 + jc);
-          step();
-          const V l0 = A[i0 * N + k], l1 = A[i1 * N + k], l2 = A[i2 * N + k], l3 = A[i3 * N + k];
-          const V u0 = A[k * N + j0], u1 = A[k * N + j1], u2 = A[k * N + j2], u3 = A[k * N + j3];
-          const V v0 = A[i0 * N + j0], v1 = A[i1 * N + j1], v2 = A[i2 * N + j2], v3 = A[i3 * N + j3];
-          A[i0 * N + j0] = v_fms(l0, u0, v0);
-          A[i1 * N + j1] = v_fms(l1, u1, v1);
-          A[i2 * N + j2] = v_fms(l2, u2, v2);
-          A[i3 * N + j3] = v_fms(l3, u3, v3);
-        }
-        for (; p < tot; p += nt) {
-          const int i = __ldg(L.ridx + r0 + ia), j = __ldg(L.cidx + c0 + jc);
-          A[i * N + j] = v_fms(A[i * N + k], A[k * N + j], A[i * N + j]);
-          step();
+          for (; p < tot; p += ntw) {
+            const int i = __ldg(L.ridx + r0 + ia), j = __ldg(ci + jc);
+            A[i * NP + j] = v_fms(A[i * NP + k], A[k * NP + j], A[i * NP + j]);
+            step();
+          }
         }
       }
       __syncthreads();
     }
     for (int t = tid; t < L.lu_nnz * S; t += nt) {
       const int e = t / S, q = t - e * S;
-      if (q < live) {
-        const T v = at(__ldg(L.l2d + e), q);
+      const int pos = __ldg(L.l2d + e);
+      if (q < live && PJ_DBG_OK(L.dbg, pos >= 0 && pos < NN, PJ_DBG_LU)) {
+        const T v = at(pos, q);
         if (nonfinite_bits(v)) bad[q] = 1;
         lu[(int64_t)e * ld + s0 + q] = v;
       }
@@ -454,7 +472,7 @@ struct LuPlan {
 
 static LuPlan lu_plan(int N, size_t esize, int64_t n) {
   LuPlan p{};
-  const size_t dense = (size_t)N * N * esize;
+  const size_t dense = (size_t)N * (size_t)(N | 1) * esize;
   const int64_t states = std::max<int64_t>(n, 1);
   if (dense <= kSmemCap) {
     p.smem = true;
@@ -471,7 +489,7 @@ static LuPlan lu_plan(int N, size_t esize, int64_t n) {
     p.dyn = dense * p.S;
     const int ctas = std::max(1, std::min(16, (int)(kSmemPerSm / (p.dyn + 1024 + 256))));
     int warps = (32 + ctas - 1) / ctas;  // 32 warps per SM where blocks of 256 allow (53 species: 11 % over 16)
-    warps = std::max(1, std::min(8, warps));
+    warps = std::max(2, std::min(8, warps));  // warp 0 finishes columns, the others update
     p.threads = 32 * warps;
     p.grid = (int)std::min<int64_t>((states + p.S - 1) / p.S, (int64_t)sm_count() * ctas);
     p.ws_bytes = 0;

@@ -114,9 +114,12 @@ int lu_build(pj_mech* m) {
     cptr[k + 1] = (int32_t)cidx.size();
   }
   // CSR entry -> dense pivot-order position
+  // dense arrays of the factorisation: rows of an odd number of entries, so
+  // that the vector accesses of one column spread over the shared-memory banks
+  const int NP = N | 1;
   std::vector<int32_t> m2d(m->nnz);
   for (int i = 0; i < N; i++)
-    for (int e = m->csr_ptr[i]; e < m->csr_ptr[i + 1]; e++) m2d[e] = pinv[i] * N + pinv[m->csr_idx[e]];
+    for (int e = m->csr_ptr[i]; e < m->csr_ptr[i + 1]; e++) m2d[e] = pinv[i] * NP + pinv[m->csr_idx[e]];
   // storage order
   m->lu_rows.clear();
   m->lu_cols.clear();
@@ -145,13 +148,14 @@ int lu_build(pj_mech* m) {
   const int lu_nnz = (int)m->lu_rows.size();
   std::vector<int32_t> l2d(lu_nnz), xcol(lu_nnz);
   for (int e = 0; e < lu_nnz; e++) {
-    l2d[e] = m->lu_rows[e] * N + m->lu_cols[e];
+    l2d[e] = m->lu_rows[e] * NP + m->lu_cols[e];
     xcol[e] = perm[m->lu_cols[e]];
   }
 
   DevLu& L = m->lu;
   L = DevLu{};
   L.N = N;
+  L.NP = NP;
   L.nnz = m->nnz;
   L.lu_nnz = lu_nnz;
   L.nl = nl;
@@ -187,6 +191,7 @@ int lu_build(pj_mech* m) {
   L.xcol = at(7);
   L.lptr = at(8);
   L.uptr = at(9);
+  L.dbg = m->dm.dbg;
   return PJ_OK;
 }
 

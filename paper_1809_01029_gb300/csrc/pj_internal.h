@@ -87,22 +87,26 @@ struct DevMech {
   int32_t has_pdep;               // some reaction depends on P (P-log, Chebyshev)
   int32_t nr_plain;               // plain reactions (kernel order): none chemically activated,
                                   // with explicit reverse parameters, P-log or Chebyshev
+  int32_t n_eff, n_rows, n_tgt;   // lengths of eff_sp / rows / each target list array
+  uint32_t* dbg;                  // error word of the bounds-checked build (PJ_DEBUG_BOUNDS)
 };
 
 // Index tables of the Newton-matrix LU (lu_symbolic.cpp, lu.cu); pivot
 // order k, dense pivot-order positions r*N + c.
 struct DevLu {
   int32_t N, nnz, lu_nnz, nl;  // nnz: CSR entries of M; nl: strictly lower factor entries
+  int32_t NP;                  // row stride of the dense pivot-order arrays (N rounded up to odd)
   const int32_t* perm;         // [N] state-vector index of pivot k
   const int32_t* rptr;         // [N+1] rows i > k of column k ...
   const int32_t* ridx;         //   ... ascending
   const int32_t* cptr;         // [N+1] columns j > k of row k ...
   const int32_t* cidx;         //   ... ascending
-  const int32_t* m2d;          // [nnz] CSR entry -> dense position
+  const int32_t* m2d;          // [nnz] CSR entry -> dense position r * NP + c
   const int32_t* l2d;          // [lu_nnz] factor entry (storage order) -> dense position
   const int32_t* xcol;         // [lu_nnz] state-vector index of the entry's column
   const int32_t* lptr;         // [N+1] lower row k in storage
   const int32_t* uptr;         // [N+1] upper row N-1-q in storage (diagonal first)
+  uint32_t* dbg;               // error word of the bounds-checked build (the mechanism's)
 };
 
 }  // namespace pj

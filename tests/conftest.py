@@ -41,3 +41,29 @@ def mechs():
             cache[name] = synth.make_mechanism(name)
         return cache[name]
     return get
+
+
+def pytest_terminal_summary(terminalreporter):
+    """How much the parity checks leaned on the oracle's rounding envelope:
+    per check, the entries that passed only through the envelope (their
+    error above rtol |ref| but within rtol env), and the well-conditioned
+    entries (env <= 10 |ref|) that met the plain per-entry bar."""
+    try:
+        from tests.parity import REPORT
+    except Exception:
+        return
+    if not REPORT:
+        return
+    tr = terminalreporter
+    ent = sum(r["entries"] for r in REPORT)
+    env = sum(r["needed_env"] for r in REPORT)
+    well = sum(r["well"] for r in REPORT)
+    worst = max(r["worst_rel_well"] for r in REPORT)
+    tr.write_sep("-", "parity checks against the oracle")
+    tr.write_line(f"{len(REPORT)} checks, {ent} entries: {env} ({100.0 * env / max(ent, 1):.2f} %) passed only "
+                  f"through the envelope; {well} ({100.0 * well / max(ent, 1):.2f} %) well-conditioned entries held "
+                  f"to rtol |ref| (largest relative error {worst:.2e})")
+    top = sorted(REPORT, key=lambda r: -r["needed_env"] / max(r["entries"], 1))[:12]
+    for r in top:
+        tr.write_line(f"  {r['needed_env']:>9} / {r['entries']:<9} via envelope, {r['well']:>9} well-conditioned "
+                      f"(max rel {r['worst_rel_well']:.1e})  {r['what']}")

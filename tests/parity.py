@@ -1,16 +1,43 @@
 """Comparison helpers for GPU-vs-oracle parity tests.
 
-Floating-point bar (stated in the benchmark spec's tolerances and derived in the
-design notes): |gpu - ref| <= rtol * max(|ref|, env) + atol, where env is the
-oracle's absolute envelope (the sum of magnitudes of the terms that make up
-the value; near chemical equilibrium net rates are differences of nearly
-equal forward and reverse rates, Sec. 3.2).  rtol = 1e-10, atol = 1e-20 for
-source terms; rtol = 1e-8 per Jacobian entry.
+Floating-point bar: |gpu - ref| <= rtol * max(|ref|, env) + atol, where env is
+the oracle's absolute envelope (the sum of magnitudes of the terms that make
+up the value; near chemical equilibrium net rates are differences of nearly
+equal forward and reverse rates, Sec. 3.2, so a correct evaluation can only
+be held to the rounding of those terms).  rtol = 1e-10, atol = 1e-20 for
+source terms; rtol = 1e-8 per Jacobian entry.  Entries whose envelope is at
+most 10 |ref| (no significant cancellation) must in addition meet the plain
+per-entry bar |gpu - ref| <= rtol |ref| + atol.  Every check records how many
+entries passed only through the envelope; the test session prints the
+totals (tests/conftest.py).
 """
+import contextlib
+import os
+
 import numpy as np
 
 RTOL_SRC, ATOL_SRC = 1e-10, 1e-20
 RTOL_JAC, ATOL_JAC = 1e-8, 1e-20
+
+# Stated accuracy of the FP32 Newton matrix M = I - h gamma J against the
+# FP64 oracle, per entry: |dM| <= NEWTON_ENTRY (|M| + h gamma env(J)) +
+# NEWTON_FLOOR.  The floor is FP32's normal range: below 2^-126 a binary32
+# value keeps fewer significant bits, and the FP32 L2 reductions that sum the
+# entries flush subnormal contributions to zero; next to M's unit diagonal
+# such entries carry no weight in a Newton step.
+NEWTON_ENTRY = 1e-5
+NEWTON_FLOOR = 64 * 2.0 ** -126
+
+
+def newton_tol(scale):
+    return NEWTON_ENTRY * np.asarray(scale) + NEWTON_FLOOR
+
+
+# one record per check_close call: what, entries, entries that passed only
+# through the envelope, well-conditioned entries, largest relative error of a
+# well-conditioned entry
+REPORT = []
+WELL = 10.0     # env <= WELL |ref|: an entry without significant cancellation
 
 
 def check_close(got, ref, env, rtol, atol, what=""):
@@ -25,7 +52,18 @@ def check_close(got, ref, env, rtol, atol, what=""):
         raise AssertionError(
             f"{what}: {bad.sum()} / {bad.size} entries out of tolerance; worst at {idx}: "
             f"gpu={got[idx]!r} ref={ref[idx]!r} env={env[idx]!r} err={err[idx]!r} tol={tol[idx]!r}")
-    needed_env = int(np.sum(err > rtol * np.abs(ref) + atol))
+    plain = rtol * np.abs(ref) + atol
+    well = env <= WELL * np.abs(ref)
+    strict_bad = well & ~(err <= plain)
+    if strict_bad.any():
+        idx = np.unravel_index(np.argmax(np.where(strict_bad, err / np.maximum(plain, 1e-300), 0)), err.shape)
+        raise AssertionError(
+            f"{what}: {strict_bad.sum()} well-conditioned entries (env <= {WELL} |ref|) beyond rtol |ref| + atol; "
+            f"worst at {idx}: gpu={got[idx]!r} ref={ref[idx]!r} env={env[idx]!r} err={err[idx]!r}")
+    needed_env = int(np.sum(err > plain))
+    rel_well = np.where(well & (ref != 0), err / np.where(ref != 0, np.abs(ref), 1.0), 0.0)
+    REPORT.append(dict(what=what, entries=int(err.size), needed_env=needed_env, well=int(well.sum()),
+                       worst_rel_well=float(rel_well.max()) if rel_well.size else 0.0))
     return needed_env
 
 
@@ -128,3 +166,21 @@ def y_envelope(m, mode, phi, par):
             if nu[k, i]:
                 ew[k] += abs(nu[k, i]) * t
     return np.concatenate([ew, fenv[:1]], axis=0)
+
+
+@contextlib.contextmanager
+def jacobian_layout(name):
+    """Run the library's Jacobian entries with one kernel family: "coop" (the
+    warps of a block share 32 states; L2-resident accumulation, rounding
+    depends on the order of cross-warp reductions) or "percore" (one state
+    per thread; bit-reproducible).  The library reads PYJAC_GB_JAC_LAYOUT at
+    every launch."""
+    old = os.environ.get("PYJAC_GB_JAC_LAYOUT")
+    os.environ["PYJAC_GB_JAC_LAYOUT"] = name
+    try:
+        yield
+    finally:
+        if old is None:
+            os.environ.pop("PYJAC_GB_JAC_LAYOUT", None)
+        else:
+            os.environ["PYJAC_GB_JAC_LAYOUT"] = old

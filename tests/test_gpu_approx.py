@@ -6,7 +6,7 @@ import pytest
 import oracle
 import synth
 from tests import tiny_mechs as tm
-from tests.parity import RTOL_JAC, ATOL_JAC, check_close
+from tests.parity import RTOL_JAC, ATOL_JAC, RTOL_SRC, ATOL_SRC, check_close, newton_tol, jacobian_layout
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,9 @@ def test_approximate_jacobian_matches_oracle(pj, mechs, name, n, mode):
     mask = oracle.sparsity_pattern(m, oracle.APPROX)
     assert np.all(Jd[~mask] == 0.0)
     pj.jacobian_dense(h, mode, d_phi, d_par, dphi=f_e)
-    assert torch.equal(f_a, f_e)
+    f_ref, f_env = oracle.source_term_envelope(m, mode, phi, par)
+    check_close(f_a.cpu().numpy(), f_ref, f_env, RTOL_SRC, ATOL_SRC, f"{name} f of the approximate form")
+    check_close(f_e.cpu().numpy(), f_ref, f_env, RTOL_SRC, ATOL_SRC, f"{name} f of the exact form")
     for fmt, conv in ((pj.PJ_CSR, oracle.dense_to_csr_values), (pj.PJ_CSC, oracle.dense_to_csc_values)):
         vals = pj.jacobian_sparse(ha, mode, d_phi, d_par, fmt=fmt).cpu().numpy()
         assert vals.shape[0] == ha.nnz
@@ -66,7 +68,7 @@ def test_approximate_jacobian_matches_oracle(pj, mechs, name, n, mode):
 
 def test_approximate_newton_matrix(pj, mechs):
     """FP32 M = I - h gamma J on the approximate pattern, at the accuracy
-    stated for the FP32 form (entries within 1e-5 of |M| + h gamma env)."""
+    stated for the FP32 form (tests/parity.py: newton_tol)."""
     m = mechs("gri53")
     ha = pj.pj_mech_create(m).with_jacobian_form(pj.PJ_JAC_APPROX)
     n = 40
@@ -81,7 +83,7 @@ def test_approximate_newton_matrix(pj, mechs):
     Ms = pj.newton_matrix_f32(ha, synth.CONP, dev(phi), dev(par), dev(hs), 1.0, fmt=pj.PJ_CSR)
     Ms = Ms.cpu().numpy().astype(np.float64)
     e = np.abs(Ms - oracle.dense_to_csr_values(m, M_ref, oracle.APPROX))
-    assert np.all(e <= 1e-5 * oracle.dense_to_csr_values(m, scale, oracle.APPROX))
+    assert np.all(e <= newton_tol(oracle.dense_to_csr_values(m, scale, oracle.APPROX)))
 
 
 def test_approximate_form_through_a_plan(pj, mechs):
@@ -98,7 +100,8 @@ def test_approximate_form_through_a_plan(pj, mechs):
         out = torch.empty((ha.nnz, n), dtype=torch.float64, device="cuda")
         f = torch.empty((m.n_species + 1, n), dtype=torch.float64, device="cuda")
         batches.append((d_par, d_phi, out, f))
-        ref.append(pj.jacobian_sparse(ha, synth.CONP, d_phi, d_par).cpu().numpy())
+        with jacobian_layout("percore"):  # the plan's one-state-per-thread arithmetic
+            ref.append(pj.jacobian_sparse(ha, synth.CONP, d_phi, d_par).cpu().numpy())
     plan = pj.Plan(ha, pj.PJ_OP_JACOBIAN, synth.CONP, batches)
     plan.run()
     torch.cuda.synchronize()

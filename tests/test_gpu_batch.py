@@ -7,9 +7,18 @@ import pytest
 
 import oracle
 import synth
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, check_close
+from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, check_close, jacobian_layout
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def percore_entry_points():
+    """The plans' persistent kernels evaluate one state per thread, as the
+    direct entry points' "percore" layout does; with that layout the two give
+    the same bits, which these tests check."""
+    with jacobian_layout("percore"):
+        yield
 
 
 @pytest.fixture(scope="module")

@@ -6,12 +6,12 @@ import pytest
 import oracle
 import synth
 from tests import tiny_mechs as tm
-from tests.parity import RTOL_SRC, ATOL_SRC, check_close, y_envelope
+from tests.parity import RTOL_SRC, ATOL_SRC, check_close, y_envelope, newton_tol
 
 pytestmark = pytest.mark.gpu
 
-# stated accuracy of the FP32 Newton matrix against the FP64 oracle
-NEWTON_ENTRY = 1e-5     # |dM| <= 1e-5 (|M| + h gamma env(J)) per entry
+# stated accuracy of the FP32 Newton matrix against the FP64 oracle: per
+# entry tests/parity.py's newton_tol; per state
 NEWTON_FRO = 1e-6       # ||dM||_F <= 1e-6 ||M||_F per state
 RTOL_VJP = 1e-8         # per output, relative to the envelope sum |u dy/dx|
 
@@ -66,14 +66,14 @@ def test_newton_matrix_f32_against_fp64_oracle(pj, mechs, name, n, gamma, mode):
     assert Md.dtype == torch.float32
     Md = Md.cpu().numpy().astype(np.float64).reshape(N1, N1, n)
     err = np.abs(Md - M_ref)
-    assert np.all(err <= NEWTON_ENTRY * scale), float(np.max(err / scale))
+    assert np.all(err <= newton_tol(scale)), float(np.max(err / newton_tol(scale)))
     fro = np.linalg.norm((Md - M_ref).reshape(-1, n), axis=0) / np.linalg.norm(M_ref.reshape(-1, n), axis=0)
     assert np.all(fro <= NEWTON_FRO), float(fro.max())
     check_close(dphi.cpu().numpy(), f_ref, f_env, RTOL_SRC, ATOL_SRC, "FP64 source terms of the Newton kernel")
     for fmt, conv in ((pj.PJ_CSR, oracle.dense_to_csr_values), (pj.PJ_CSC, oracle.dense_to_csc_values)):
         Ms = pj.newton_matrix_f32(h, mode, d_phi, d_par, d_h, gamma, fmt=fmt).cpu().numpy().astype(np.float64)
         e = np.abs(Ms - conv(m, M_ref))
-        assert np.all(e <= NEWTON_ENTRY * conv(m, scale)), (fmt, float(np.max(e / conv(m, scale))))
+        assert np.all(e <= newton_tol(conv(m, scale))), (fmt, float(np.max(e / newton_tol(conv(m, scale)))))
 
 
 @pytest.mark.parametrize("mode", [synth.CONP, synth.CONV])
@@ -165,3 +165,40 @@ def test_autograd_function_matches_finite_differences(pj, mechs):
             fd = (vals[0] - vals[1]) / (2 * step)
             tol = 1e-4 * e_th[i, p] + 1e-10 * np.sum(np.abs(u) * y_envelope(m, synth.CONP, phi, par)) / step
             assert abs(fd - g_th[i, p]) <= tol, (i, p, fd, g_th[i, p])
+
+
+def test_autograd_function_follows_theta(pj, mechs):
+    """A theta that differs from the mechanism's parameters moves the
+    evaluation point: y and both gradients equal the oracle's on a mechanism
+    holding theta's (ln A, beta, Ea); theta equal to the mechanism's gives
+    the mechanism's own values."""
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m)
+    n = 40
+    phi, par = synth.make_states(m, n, 23, synth.CONP)
+    uw, uT = synth.make_cotangents(m.n_species, n, 23)
+    u = np.concatenate([uw, uT[None, :]], axis=0)
+    rng = np.random.default_rng(3)
+    th0 = pj.arrhenius_parameters(m).numpy()
+    th = th0.copy()
+    th[:, 0] += rng.normal(0.0, 0.3, m.n_reactions)
+    th[:, 1] += rng.normal(0.0, 0.05, m.n_reactions)
+    th[:, 2] *= np.exp(rng.normal(0.0, 0.02, m.n_reactions))
+    mp = m.copy()
+    mp.A, mp.beta, mp.Ea = np.exp(th[:, 0]), th[:, 1].copy(), th[:, 2].copy()
+    for theta_np, ref_m in ((th, mp), (th0, m)):
+        theta = torch.from_numpy(theta_np.copy()).cuda().requires_grad_(True)
+        d_phi = dev(phi).requires_grad_(True)
+        y = pj.source_terms_y(h, synth.CONP, d_phi, dev(par), theta)
+        (y * dev(u)).sum().backward()
+        y_ref = oracle.outputs_y(ref_m, synth.CONP, phi, par)
+        check_close(y.detach().cpu().numpy(), y_ref, y_envelope(ref_m, synth.CONP, phi, par), RTOL_SRC, ATOL_SRC,
+                    "y at theta")
+        g_phi, g_th = oracle.vjp(ref_m, synth.CONP, phi, par, uw, uT)
+        e_phi, e_th = oracle.vjp_envelope(ref_m, synth.CONP, phi, par, uw, uT)
+        check_close(d_phi.grad.cpu().numpy(), g_phi, e_phi, RTOL_VJP, 0.0, "g_phi at theta")
+        check_close(theta.grad.cpu().numpy(), g_th, e_th, RTOL_VJP, 0.0, "g_theta at theta")
+    # the perturbation is large enough to matter
+    assert not np.allclose(oracle.outputs_y(mp, synth.CONP, phi, par), oracle.outputs_y(m, synth.CONP, phi, par),
+                           rtol=1e-3)

@@ -11,11 +11,10 @@ import pytest
 
 import oracle
 import synth
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope
+from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope, paper_error_norms, newton_tol
 
 pytestmark = pytest.mark.gpu
 
-NEWTON_ENTRY = 1e-5     # the FP32 Newton matrix's stated per-entry accuracy
 RTOL_VJP = 1e-8
 
 
@@ -82,7 +81,12 @@ def test_gri53_one_mebi_states_source_and_jacobians(pj, mechs, mode):
     torch.cuda.empty_cache()
     jd = torch.empty((N1 * N1, n), dtype=torch.float64, device="cuda")
     pj.pj_eval_jacobian_dense(h, mode, n, par, phi, n, jd, dphi, status, w, wb, stream)
-    check_close(_cols(torch, jd, idx).reshape(N1, N1, -1), J, env, RTOL_JAC, ATOL_JAC, "dense, 1 Mi states")
+    Jd = _cols(torch, jd, idx).reshape(N1, N1, -1)
+    check_close(Jd, J, env, RTOL_JAC, ATOL_JAC, "dense, 1 Mi states")
+    # the paper's norms (Sec. 3.3): E_L, and E_C at the relaxed threshold
+    # C = 1e15 against the largest value the paper reports there (4.5e-5)
+    EL, EC = paper_error_norms(Jd, J, C_thresh=1e15)
+    assert EL < 1e-10 and EC < 4.5e-5, (EL, EC)
     assert int(status.item()) == 0
     del jd, w, dphi
     torch.cuda.empty_cache()
@@ -159,7 +163,7 @@ def test_usc111_quarter_mebi_states_newton_and_jacobian(pj, mechs):
     got = _cols(torch, M, idx[keep]).astype(np.float64)
     conv = lambda a: oracle.dense_to_csr_values(m, a)
     err = np.abs(got - conv(M_ref[..., keep]))
-    tol = NEWTON_ENTRY * conv(scale[..., keep])
+    tol = newton_tol(conv(scale[..., keep]))
     assert np.all(err <= tol), float(np.max(err / tol))
     del M
     Jd = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
@@ -207,16 +211,24 @@ def test_gri53_vjp_65536_states(pj, mechs):
 
 
 def test_ic5874_ragged_batches_in_one_plan(pj, mechs):
-    """874 species / 3796 reactions, the 32 log-uniform batches (623,411
-    states) through one plan of persistent kernels in groups sharing an output
-    pool, replayed from a captured graph: source terms and sampled Jacobian
-    columns of states of several batches."""
+    """874 species / 3796 reactions: the 32 log-uniform batches (623,411
+    states) through one plan of persistent kernels in the benchmark's groups,
+    replayed from a captured graph.  All outputs together (523 GB) exceed
+    the device, so the two smallest batches of every group get output
+    regions of their own and the other batches of a group share one scratch
+    region; every group's checked batches survive the replay.  Source terms
+    and all 875 Jacobian columns of 18 states (three of each checked batch:
+    first, middle, last) against the oracle with the envelope rule, the
+    oracle's columns spread over a spawned process pool."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
     import torch
     m = mechs("ic5874")
     h = pj.pj_mech_create(m)
     N1 = m.n_species + 1
     sizes = [int(x) for x in synth.ragged_batch_sizes()]
-    group_states = 140000
+    group_states = 240000                     # the benchmark's grouping
     groups, cur, acc = [], [], 0
     for b, nb in enumerate(sizes):
         if cur and acc + nb > group_states:
@@ -225,48 +237,55 @@ def test_ic5874_ragged_batches_in_one_plan(pj, mechs):
         cur.append(b)
         acc += nb
     groups.append(cur)
-    pool_states = max(sum(sizes[b] for b in g) for g in groups)
-    pool = torch.empty(pool_states * h.nnz, dtype=torch.float64, device="cuda")
-    fpool = torch.empty(pool_states * N1, dtype=torch.float64, device="cuda")
-    # the groups share the pool, so the last group's outputs are the ones
-    # left after the replay: its first and last batches are checked
-    last = groups[-1]
-    check = {last[0], last[-1]}
-    batches, host = [], {}
+    assert len(groups) >= 2
+    check = set()
     for g in groups:
-        off = 0
-        for b in g:
-            nb = sizes[b]
-            phi_h, par_h = synth.make_states(m, nb, 2018 + 5 + 7919 * b, synth.CONP)
-            if b in check:
-                host[b] = (phi_h, par_h)
-            o = pool[off * h.nnz:(off + nb) * h.nnz].view(h.nnz, nb)
-            f = fpool[off * N1:(off + nb) * N1].view(N1, nb)
-            batches.append((_dev(torch, par_h), _dev(torch, phi_h), o, f))
-            off += nb
+        check.update(sorted(g, key=lambda b: sizes[b])[:2])
+    scratch_states = max(sizes[b] for b in range(len(sizes)) if b not in check)
+    scratch = torch.empty(scratch_states * h.nnz, dtype=torch.float64, device="cuda")
+    fscratch = torch.empty(scratch_states * N1, dtype=torch.float64, device="cuda")
+    batches, host = [], {}
+    for b, nb in enumerate(sizes):
+        phi_h, par_h = synth.make_states(m, nb, 2018 + 5 + 7919 * b, synth.CONP)
+        if b in check:
+            host[b] = (phi_h, par_h)
+            o = torch.full((h.nnz, nb), float("nan"), dtype=torch.float64, device="cuda")
+            f = torch.full((N1, nb), float("nan"), dtype=torch.float64, device="cuda")
+        else:
+            o = scratch[: nb * h.nnz].view(h.nnz, nb)
+            f = fscratch[: nb * N1].view(N1, nb)
+        batches.append((_dev(torch, par_h), _dev(torch, phi_h), o, f))
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     plan = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, batches, max_states_per_launch=group_states, status=status)
+    assert plan.config()["groups"] == len(groups)
     plan.set_config(128, 8, 0)
     gs = torch.cuda.Stream()
     plan.capture(gs)
     plan.launch(gs)
     gs.synchronize()
     assert int(status.item()) == 0
-    rp, ci = h.sparsity(pj.PJ_CSR)
-    rows = np.repeat(np.arange(N1), np.diff(rp))
-    cols = [0, 1, 2, 300, 873]
+    phis, pars, vals, fs = [], [], [], []
     for b in sorted(check):
         phi_h, par_h = host[b]
         _, _, o, f = batches[b]
-        idx = np.unique([0, 33, sizes[b] // 2, sizes[b] - 1])
-        ps, qs = phi_h[:, idx], par_h[idx]
-        ref, env = oracle.source_term_envelope(m, synth.CONP, ps, qs)
-        check_close(_cols(torch, f, idx), ref, env, RTOL_SRC, ATOL_SRC, f"874 species, batch {b}")
-        Jc = oracle.jacobian_columns(m, synth.CONP, ps, qs, cols)
-        dense = np.zeros((N1, N1, len(idx)))
-        dense[rows, ci] = _cols(torch, o, idx)
-        got = dense[:, cols]
-        scale = np.max(np.abs(Jc), axis=0, keepdims=True)
-        assert np.all(np.abs(got - Jc) <= RTOL_JAC * np.abs(Jc) + 1e-12 * scale), b
-    del plan, batches, pool, fpool
+        idx = np.unique([0, sizes[b] // 2, sizes[b] - 1])
+        phis.append(phi_h[:, idx])
+        pars.append(par_h[idx])
+        vals.append(_cols(torch, o, idx))
+        fs.append(_cols(torch, f, idx))
+    del plan, batches, scratch, fscratch
     torch.cuda.empty_cache()
+    ps, qs = np.concatenate(phis, axis=1), np.concatenate(pars)
+    vals, fs = np.concatenate(vals, axis=1), np.concatenate(fs, axis=1)
+    assert ps.shape[1] >= 16
+    ref, env = oracle.source_term_envelope(m, synth.CONP, ps, qs)
+    check_close(fs, ref, env, RTOL_SRC, ATOL_SRC, "874 species source terms, every group")
+    workers = max(1, min(os.cpu_count() or 1, 32))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        J, envJ = oracle.jacobian_envelope(m, synth.CONP, ps, qs, map_fn=ex.map, chunks=4 * workers)
+    check_close(vals, oracle.dense_to_csr_values(m, J), oracle.dense_to_csr_values(m, envJ), RTOL_JAC, ATOL_JAC,
+                "874 species CSR Jacobian, all columns, every group")
+    # the paper's norms (Sec. 3.3) over the sampled states: E_L, and E_C at the
+    # relaxed threshold against the largest value the paper reports there
+    EL, EC = paper_error_norms(vals, oracle.dense_to_csr_values(m, J), C_thresh=1e15)
+    assert EL < 1e-10 and EC < 4.5e-5, (EL, EC)

@@ -6,7 +6,7 @@ import pytest
 import oracle
 import synth
 from tests import tiny_mechs as tm
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, paper_error_norms
+from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, paper_error_norms, jacobian_layout
 
 pytestmark = pytest.mark.gpu
 
@@ -77,8 +77,12 @@ def test_jacobian_all_formats_match_oracle(pj, mechs, name, n, mode):
     for fmt, conv in ((pj.PJ_CSR, oracle.dense_to_csr_values), (pj.PJ_CSC, oracle.dense_to_csc_values)):
         vals = pj.jacobian_sparse(h, mode, d_phi, d_par, fmt=fmt).cpu().numpy()
         check_close(vals, conv(m, J), conv(m, env), RTOL_JAC, ATOL_JAC, f"{name} fmt={fmt} mode={mode}")
-    EL, EC = paper_error_norms(Jd, J)
+    # the paper's norms (Sec. 3.3): LAPACK-style E_L, and the filtered E_C at
+    # the relaxed threshold C = 1e15 against the largest value the paper
+    # reports for its own Jacobians at that threshold (4.5e-5)
+    EL, EC = paper_error_norms(Jd, J, C_thresh=1e15)
     assert EL < 1e-10
+    assert EC < 4.5e-5, EC
 
 
 def test_invalid_states_give_nan_and_count(pj, mechs):
@@ -135,20 +139,34 @@ def test_state_at_T_mid_and_boundaries(pj, mechs):
                 "T boundaries jacobian")
 
 
-def test_sharding_by_offset_equals_one_launch(pj, mechs):
+@pytest.mark.parametrize("layout", ["percore", "coop"])
+def test_sharding_by_offset_equals_one_launch(pj, mechs, layout):
     """Replicas-only multi-GPU: a shard is (pointer offset, n).  Evaluating a
-    batch shard by shard gives the same bits as one launch."""
+    batch shard by shard gives the same bits as one launch with the
+    one-state-per-thread layout; with the cooperative layout (cross-warp
+    reductions in any order) the same values to the rounding of the sums,
+    checked against the oracle's envelope on every 25th state."""
     import torch
     m = mechs("gri53")
     h = pj.pj_mech_create(m)
     n = 1000
     phi, par = synth.make_states(m, n, 31, synth.CONP)
     d_phi, d_par = to_dev(phi), to_dev(par)
-    whole = pj.jacobian_sparse(h, synth.CONP, d_phi, d_par)
-    parts = []
-    for lo, hi in ((0, 333), (333, 640), (640, 1000)):
-        parts.append(pj.jacobian_sparse(h, synth.CONP, d_phi[:, lo:hi], d_par[lo:hi]))
-    assert torch.equal(whole, torch.cat(parts, dim=1))
+    with jacobian_layout(layout):
+        whole = pj.jacobian_sparse(h, synth.CONP, d_phi, d_par)
+        parts = []
+        for lo, hi in ((0, 333), (333, 640), (640, 1000)):
+            parts.append(pj.jacobian_sparse(h, synth.CONP, d_phi[:, lo:hi], d_par[lo:hi]))
+    cat = torch.cat(parts, dim=1)
+    if layout == "percore":
+        assert torch.equal(whole, cat)
+        return
+    pick = np.arange(0, n, 25)
+    J, env = oracle.jacobian_envelope(m, synth.CONP, phi[:, pick], par[pick])
+    ref, env = oracle.dense_to_csr_values(m, J), oracle.dense_to_csr_values(m, env)
+    for got, what in ((whole, "one launch"), (cat, "shards")):
+        check_close(got.cpu().numpy()[:, pick], ref, env, RTOL_JAC, ATOL_JAC, what)
+    check_close(cat.cpu().numpy()[:, pick], whole.cpu().numpy()[:, pick], env, 1e-13, 0.0, "shards vs one launch")
 
 
 def test_jacobian_requires_source_term_buffer(pj, mechs):
@@ -176,15 +194,46 @@ def test_mechanism_file_gives_identical_results(pj, mechs, tmp_path):
         phi, par = synth.make_states(m, 300, 4 + mode, mode)
         d_phi, d_par = to_dev(phi), to_dev(par)
         assert torch.equal(pj.source_terms(h1, mode, d_phi, d_par), pj.source_terms(h2, mode, d_phi, d_par))
-        assert torch.equal(pj.jacobian_sparse(h1, mode, d_phi, d_par), pj.jacobian_sparse(h2, mode, d_phi, d_par))
+        with jacobian_layout("percore"):  # bit-reproducible layout
+            assert torch.equal(pj.jacobian_sparse(h1, mode, d_phi, d_par), pj.jacobian_sparse(h2, mode, d_phi, d_par))
 
 
 @pytest.mark.parametrize("fmt", ["csr", "csc"])
 def test_host_buffer_entry_equals_device_entry(pj, mechs, fmt):
     """pj_eval_jacobian_sparse_host (host buffers, chunked and overlapped
-    transfers) gives the device entry's bits: several chunks with a ragged
-    last one from page-locked buffers, one chunk from pageable numpy arrays,
-    and the invalid-state count."""
+    transfers) gives the device entry's bits (both with the bit-reproducible
+    one-state-per-thread layout): several chunks with a ragged last one from
+    page-locked buffers, one chunk from pageable numpy arrays, and the
+    invalid-state count."""
+    with jacobian_layout("percore"):
+        _host_entry_case(pj, mechs, fmt)
+
+
+def test_host_buffer_entry_cooperative_layout(pj, mechs):
+    """The host-buffer entry with the default (cooperative) layout: the same
+    NaN pattern and invalid-state count as the device entry, values against
+    the oracle on sampled states of every chunk."""
+    import torch
+    m = mechs("gri53")
+    h = pj.pj_mech_create(m)
+    n = 3000
+    phi, par = synth.make_states(m, n, 62, synth.CONP)
+    phi[0, 2100] = -1.0
+    with jacobian_layout("coop"):
+        vals, dphi, bad = pj.jacobian_sparse_host(h, synth.CONP, torch.from_numpy(phi), torch.from_numpy(par),
+                                                  chunk=1024)
+    assert bad == 1
+    vals, dphi = vals.numpy(), dphi.numpy()
+    assert np.isnan(vals[:, 2100]).all() and np.isnan(dphi[:, 2100]).all()
+    pick = np.array([0, 511, 1023, 1024, 1500, 2047, 2048, 2999])
+    J, env = oracle.jacobian_envelope(m, synth.CONP, phi[:, pick], par[pick])
+    check_close(vals[:, pick], oracle.dense_to_csr_values(m, J), oracle.dense_to_csr_values(m, env), RTOL_JAC,
+                ATOL_JAC, "host entry, cooperative layout")
+    f_ref, f_env = oracle.source_term_envelope(m, synth.CONP, phi[:, pick], par[pick])
+    check_close(dphi[:, pick], f_ref, f_env, RTOL_SRC, ATOL_SRC, "host entry source terms")
+
+
+def _host_entry_case(pj, mechs, fmt):
     import torch
     m = mechs("gri53")
     h = pj.pj_mech_create(m)

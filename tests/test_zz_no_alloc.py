@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close
+from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, jacobian_layout
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,10 @@ def test_noalloc_matches_regular_entry_point_on_two_calls(mechs, name, n, mode, 
     work = torch.empty(max(wb, 1), dtype=torch.uint8, device="cuda")
     ref = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")
     ref_f = torch.empty((N1, n), dtype=torch.float64, device="cuda")
-    pj.pj_eval_jacobian_sparse(h, mode, fmt, n, d_par, d_phi, n, ref, ref_f, None, work, wb)
+    # the regular entry's one-state-per-thread layout runs the same arithmetic
+    # in the same order as this entry point
+    with jacobian_layout("percore"):
+        pj.pj_eval_jacobian_sparse(h, mode, fmt, n, d_par, d_phi, n, ref, ref_f, None, work, wb)
     ref = ref.cpu().numpy()
     ref_f = ref_f.cpu().numpy()
     assert np.all(np.isfinite(ref))

@@ -54,7 +54,9 @@ extern "C" {
 #define PJ_ERR_CUDA 3         /* a CUDA runtime call or launch failed */
 #define PJ_ERR_NOMEM 4        /* host or device allocation failed / workspace too small */
 #define PJ_ERR_UNSUPPORTED 5  /* valid request this build does not handle */
-#define PJ_ERR_TIMEOUT 6      /* a bounded device-side wait gave up */
+#define PJ_ERR_TIMEOUT 6      /* reserved for a bounded device-side wait that gives up; no entry point of
+                                 this build returns it (its kernels wait only at block barriers and in
+                                 tcgen05.alloc, whose columns are always available by construction) */
 
 /* evaluation assumption (Sec. 2.2) */
 #define PJ_CONP 0
@@ -200,6 +202,26 @@ int pj_mech_with_jacobian_form(const pj_mech* mech, int form, pj_mech** out);
 /* The Jacobian form of a handle (PJ_JAC_EXACT for pj_mech_create/load). */
 int pj_mech_jacobian_form(const pj_mech* mech, int32_t* form);
 
+/* The high-pressure (or only) modified-Arrhenius parameters of every
+ * reaction (the forward rate constant of Sec. 2.2, k = A T^beta
+ * exp(-Ea / (R T))), in the reaction order of the description: host arrays
+ * h_lnA[Nr] (ln A), h_beta[Nr], h_Ea[Nr] (cal/mol), written by the call.
+ * These are the parameters theta of the VJP's g_theta (pj_vjp).  Errors:
+ * PJ_ERR_ARG (null). */
+int pj_mech_arrhenius(const pj_mech* mech, double* h_lnA, double* h_beta, double* h_Ea);
+
+/* A new handle for the same mechanism (and Jacobian form) with reaction i's
+ * high-pressure (or only) Arrhenius parameters replaced by (h_lnA[i],
+ * h_beta[i], h_Ea[i]) (Sec. 2.2 rate constants; host arrays of Nr, read
+ * only; the low-pressure, reverse, P-log and Chebyshev data stay as they
+ * are).  For parameter fitting and sensitivity loops that evaluate the
+ * source terms and the VJP at changing theta.  The source handle is not
+ * modified; release *out with pj_mech_free().  Errors: PJ_ERR_ARG (null,
+ * non-finite parameter), PJ_ERR_MECH (exp(ln A) not a positive finite
+ * number), PJ_ERR_CUDA / PJ_ERR_NOMEM (upload). */
+int pj_mech_with_arrhenius(const pj_mech* mech, const double* h_lnA, const double* h_beta, const double* h_Ea,
+                           pj_mech** out);
+
 /* Sparsity pattern of the Jacobian (Sec. 3.4), identical for CONP and
  * CONV: rows/columns of T and S dense, diagonal kept, species row k has
  * column j when a reaction that changes k has a rate depending on j (its
@@ -225,7 +247,20 @@ int pj_eval_source_terms(const pj_mech* mech, int mode, int64_t n, const double*
  * (PJ_CSC) value order: d_vals[e*ld + s].  d_dphi (required, same layout as
  * d_phi) receives the source terms, which the Jacobian kernel computes on the
  * way.  d_work must point to pj_workspace_size(PJ_OP_JACOBIAN) bytes of
- * device memory (may be NULL when that size is 0). */
+ * device memory (may be NULL when that size is 0).  That size is the need of
+ * the one-state-per-thread layouts, the largest of any layout; the
+ * cooperative layout uses no workspace, so a short one is rejected
+ * (PJ_ERR_NOMEM, nothing launched) only when the layout that runs needs it.
+ *
+ * Reproducibility: with the cooperative layout (pj_jacobian_layout) the
+ * entries and production rates receive reductions from several warps in an
+ * order that can change between runs, so results agree to the rounding of
+ * those sums, not bit for bit; the one-state-per-thread layouts give the
+ * same bits on every run.  The environment variable PYJAC_GB_JAC_LAYOUT
+ * (read at every launch) forces a family: "percore" (bit-reproducible) or
+ * "coop" (where its shared memory fits); PYJAC_GB_COOP_WARPS = 4, 8 or 16
+ * sets the cooperative block's warps and PYJAC_GB_COOP_CTAS the blocks per
+ * SM. */
 int pj_eval_jacobian_sparse(const pj_mech* mech, int mode, int fmt, int64_t n,
                             const double* d_param, const double* d_phi, int64_t ld,
                             double* d_vals, double* d_dphi, int* d_status,
@@ -256,9 +291,15 @@ int pj_newton_matrix_f32(const pj_mech* mech, int mode, int fmt, int64_t n, cons
  * working arrays live in a fixed 64 MiB device array inside the library,
  * which every GPU that loads the library holds until the process exits.
  * Same arguments and outputs as pj_eval_jacobian_sparse minus the workspace.
- *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress, with the device current); make that first call
+ *  - Every call looks up that array's device address in the current
+ *    device's context (cudaGetSymbolAddress, which does not allocate); the
+ *    first call on a device loads the library's module there, so make it
  *    before any stream capture.
+ *  - It runs the one-state-per-thread kernel with every per-state array in
+ *    that global array (none of the shared-memory, tensor-memory or
+ *    cooperative layouts pj_eval_jacobian_sparse picks), so it is slower
+ *    than the regular entry on mechanisms those layouts serve (the
+ *    benchmark's variants report both).
  *  - All calls on a device share the array and it keeps the last call's
  *    contents; calls that overlap on the GPU (different streams, or
  *    concurrent host threads) race on it, so serialise them.
@@ -289,6 +330,47 @@ int pj_eval_jacobian_sparse_noalloc(const pj_mech* mech, int mode, int fmt, int6
 int pj_eval_jacobian_sparse_host(const pj_mech* mech, int mode, int fmt, int64_t n, const double* h_param,
                                  const double* h_phi, double* h_vals, double* h_dphi, int* h_status, int64_t chunk,
                                  void* stream);
+
+/* Bounds-checked build.  The library compiled with -DPJ_DEBUG_BOUNDS
+ * (paper_1809_01029_gb300.build: debug_bounds=True, libpyjac_gb_dbg.so)
+ * checks every lookup in the index tables derived at mechanism load (the
+ * Jacobian kernels' per-reaction target lists and full -> sparse position
+ * maps, the species-row and efficiency lists, the LU scatter and gather
+ * maps) before use; a bad index sets a bit of the mechanism's device error
+ * word and the access is skipped (no trap).  Bits: 1 target list, 2 position
+ * map, 4 species-row list, 8 efficiency list, 16 LU map.  The paper has no
+ * counterpart (it is a diagnostic of this library).
+ *
+ * pj_debug_word: *h_word = the error word (synchronous copy; clear != 0
+ * resets it).  Always 0 in the regular build.  Errors: PJ_ERR_ARG,
+ * PJ_ERR_CUDA.
+ * pj_debug_build: *on = 1 in the bounds-checked build, else 0.
+ * pj_debug_set_target: test hook of the bounds-checked build only -- writes
+ * `value` into entry `index` of the device target list of fmt (PJ_CSR or
+ * PJ_CSC), so that a test can show the checks catching a corrupt table.
+ * PJ_ERR_UNSUPPORTED in the regular build; PJ_ERR_ARG for an index outside
+ * the list. */
+int pj_debug_word(const pj_mech* mech, uint32_t* h_word, int clear);
+int pj_debug_build(int32_t* on);
+int pj_debug_set_target(const pj_mech* mech, int fmt, int32_t index, int32_t value);
+
+/* Kernel layouts of the Jacobian entries (pj_jacobian_layout) */
+#define PJ_LAYOUT_PERCORE 0  /* one state per thread; state arrays in shared memory or a workspace */
+#define PJ_LAYOUT_TMEM 1     /* one state per thread; h_k/RT in tensor memory */
+#define PJ_LAYOUT_COOP 2     /* the warps of a block share 32 states and split the reactions */
+
+/* The kernel layout the Jacobian entries (pj_eval_jacobian_sparse / dense,
+ * fmt PJ_CSR, PJ_CSC or PJ_DENSE) and the FP32 Newton matrix (prec PJ_F32)
+ * use for n states of this mechanism on the current device: *layout =
+ * PJ_LAYOUT_*.  The choice was measured on GB300: the cooperative layout for
+ * batches below one round of the one-state-per-thread kernels, for
+ * mechanisms whose one-state-per-thread arrays would live in a global
+ * workspace, and for the FP32 form at sizes that use tensor memory; the
+ * one-state-per-thread layouts otherwise.  The cooperative layout keeps few
+ * Jacobians live in L2 (a third of the DRAM traffic at 53 species) and is
+ * not bit-reproducible (see pj_eval_jacobian_sparse).  Errors: PJ_ERR_ARG,
+ * PJ_ERR_CUDA (no device copy). */
+int pj_jacobian_layout(const pj_mech* mech, int fmt, int prec, int64_t n, int32_t* layout);
 
 /* operation ids for pj_workspace_size */
 #define PJ_OP_SOURCE 0

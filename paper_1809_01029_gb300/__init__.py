@@ -3,6 +3,9 @@ chemical-kinetic Jacobians (arXiv:1809.01029), behind the C ABI of
 include/pyjac_gb.h.  This package is the thin Python binding."""
 from .api import (Mechanism, pj_mech_create, pj_mech_load, pj_sparsity, pj_workspace_size,
                   pj_mech_with_jacobian_form, pj_mech_jacobian_form, PJ_JAC_EXACT, PJ_JAC_APPROX,
+                  pj_mech_arrhenius, pj_mech_with_arrhenius, pj_jacobian_layout,
+                  pj_debug_word, pj_debug_build, pj_debug_set_target,
+                  PJ_LAYOUT_PERCORE, PJ_LAYOUT_TMEM, PJ_LAYOUT_COOP,
                   pj_lu_factor, pj_lu_solve, lu_factor, lu_solve, PJ_OP_LU, PJ_F64, PJ_F32,
                   pj_eval_source_terms, pj_eval_jacobian_sparse, pj_eval_jacobian_dense,
                   pj_eval_jacobian_sparse_noalloc, pj_eval_jacobian_sparse_host, jacobian_sparse_host,

@@ -18,6 +18,7 @@ PJ_OP_SOURCE, PJ_OP_JACOBIAN, PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_
 PJ_F64, PJ_F32 = 0, 1
 PJ_MAX_SP = 4
 PJ_JAC_EXACT, PJ_JAC_APPROX = 0, 1
+PJ_LAYOUT_PERCORE, PJ_LAYOUT_TMEM, PJ_LAYOUT_COOP = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -52,6 +53,12 @@ SIGNATURES = {
     "pj_sparsity": (C.c_int, [_vp, C.c_int, _ip, _ip]),
     "pj_mech_with_jacobian_form": (C.c_int, [_vp, C.c_int, C.POINTER(_vp)]),
     "pj_mech_jacobian_form": (C.c_int, [_vp, _ip]),
+    "pj_mech_arrhenius": (C.c_int, [_vp, _dp, _dp, _dp]),
+    "pj_jacobian_layout": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _ip]),
+    "pj_debug_word": (C.c_int, [_vp, C.POINTER(C.c_uint32), C.c_int]),
+    "pj_debug_build": (C.c_int, [_ip]),
+    "pj_debug_set_target": (C.c_int, [_vp, C.c_int, C.c_int32, C.c_int32]),
+    "pj_mech_with_arrhenius": (C.c_int, [_vp, _dp, _dp, _dp, C.POINTER(_vp)]),
     "pj_eval_source_terms": (C.c_int, [_vp, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp, _vp,
                                        _vp, C.c_size_t, _vp]),
     "pj_eval_jacobian_sparse": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int64, _vp, _vp, C.c_int64, _vp,
@@ -92,7 +99,9 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library this process loads: the in-tree build, or the one named by
+    PYJAC_GB_LIB (e.g. the bounds-checked build libpyjac_gb_dbg.so)."""
+    return os.environ.get("PYJAC_GB_LIB") or _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -100,7 +109,7 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
     if not os.path.exists(path):
         if build_if_missing:
             _build.build()

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _native as N
 from ._native import (PJ_CONP, PJ_CONV, PJ_CSR, PJ_CSC, PJ_DENSE, PJ_OP_SOURCE, PJ_OP_JACOBIAN,
-                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_LU, PJ_F64, PJ_F32, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX, check)
+                      PJ_OP_NEWTON, PJ_OP_VJP, PJ_OP_Y, PJ_OP_FD, PJ_OP_LU, PJ_F64, PJ_F32, PJ_MAX_SP, PJ_JAC_EXACT, PJ_JAC_APPROX,
+                      PJ_LAYOUT_PERCORE, PJ_LAYOUT_TMEM, PJ_LAYOUT_COOP, check)
 
 
 def _ptr(t):
@@ -67,6 +68,33 @@ class Mechanism:
         (PJ_JAC_APPROX, Sec. 3.4) Jacobian and its pattern."""
         h = C.c_void_p()
         check(N.load().pj_mech_with_jacobian_form(self._h, form, C.byref(h)), "pj_mech_with_jacobian_form")
+        return Mechanism(h, self.name)
+
+    def jacobian_layout(self, fmt=PJ_CSR, prec=PJ_F64, n=1 << 20):
+        """PJ_LAYOUT_PERCORE / _TMEM / _COOP: the kernel layout of the
+        Jacobian entries for n states of this mechanism on the current device."""
+        lay = C.c_int32()
+        check(N.load().pj_jacobian_layout(self._h, fmt, prec, int(n), C.byref(lay)), "pj_jacobian_layout")
+        return lay.value
+
+    def arrhenius(self):
+        """(ln A, beta, Ea) [Nr] each: the high-pressure (or only) Arrhenius
+        parameters of the handle, in reaction order (float64 numpy)."""
+        nr = self.n_reactions
+        a, b, e = (np.zeros(max(nr, 1)) for _ in range(3))
+        check(N.load().pj_mech_arrhenius(self._h, a.ctypes.data_as(N._dp), b.ctypes.data_as(N._dp),
+                                         e.ctypes.data_as(N._dp)), "pj_mech_arrhenius")
+        return a[:nr], b[:nr], e[:nr]
+
+    def with_arrhenius(self, lnA, beta, Ea) -> "Mechanism":
+        """The same mechanism with the high-pressure (or only) Arrhenius
+        parameters replaced (Sec. 2.2 rate constants)."""
+        a, b, e = (np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1)) for x in (lnA, beta, Ea))
+        if not (a.shape == b.shape == e.shape == (self.n_reactions,)):
+            raise ValueError(f"lnA, beta and Ea must each hold {self.n_reactions} values")
+        h = C.c_void_p()
+        check(N.load().pj_mech_with_arrhenius(self._h, a.ctypes.data_as(N._dp), b.ctypes.data_as(N._dp),
+                                              e.ctypes.data_as(N._dp), C.byref(h)), "pj_mech_with_arrhenius")
         return Mechanism(h, self.name)
 
     def sparsity(self, fmt=PJ_CSR):
@@ -159,6 +187,36 @@ def pj_mech_load(path: str) -> Mechanism:
 
 def pj_mech_with_jacobian_form(mech: Mechanism, form) -> Mechanism:
     return mech.with_jacobian_form(form)
+
+
+def pj_debug_word(mech: Mechanism, clear=False) -> int:
+    """The bounds-checked build's device error word of mech (0 when every
+    index-table lookup stayed in range; always 0 in the regular build)."""
+    w = C.c_uint32()
+    check(N.load().pj_debug_word(mech.handle, C.byref(w), int(bool(clear))), "pj_debug_word")
+    return w.value
+
+
+def pj_debug_build() -> bool:
+    on = C.c_int32()
+    check(N.load().pj_debug_build(C.byref(on)), "pj_debug_build")
+    return bool(on.value)
+
+
+def pj_debug_set_target(mech: Mechanism, fmt, index, value):
+    return check(N.load().pj_debug_set_target(mech.handle, fmt, int(index), int(value)), "pj_debug_set_target")
+
+
+def pj_jacobian_layout(mech: Mechanism, fmt=PJ_CSR, prec=PJ_F64, n=1 << 20):
+    return mech.jacobian_layout(fmt, prec, n)
+
+
+def pj_mech_arrhenius(mech: Mechanism):
+    return mech.arrhenius()
+
+
+def pj_mech_with_arrhenius(mech: Mechanism, lnA, beta, Ea) -> Mechanism:
+    return mech.with_arrhenius(lnA, beta, Ea)
 
 
 def pj_mech_jacobian_form(mech: Mechanism):
@@ -278,6 +336,17 @@ def _check_batch(mech, phi, param):
     return phi.shape[1], max(phi.stride(0), 1)
 
 
+def _check_out(t, rows, ld, n, dtype, what):
+    """A caller-given output must be [rows, n] on the states' device with the
+    states' leading dimension (the C ABI takes one ld for all arrays)."""
+    if t is None:
+        return
+    if t.dtype != dtype or not t.is_cuda or t.dim() != 2 or t.shape[0] != rows or t.shape[1] != n:
+        raise ValueError(f"{what} must be a CUDA {dtype} tensor of shape [{rows}, {n}]")
+    if t.stride(1) != 1 or (rows > 1 and t.stride(0) != ld):
+        raise ValueError(f"{what} must have unit stride along states and leading dimension {ld} (that of phi)")
+
+
 def _workspace(mech, op, n, device):
     import torch
     b = mech.workspace_size(op, n)
@@ -287,6 +356,7 @@ def _workspace(mech, op, n, device):
 def source_terms(mech, mode, phi, param, out=None, status=None, stream=None):
     import torch
     n, ld = _check_batch(mech, phi, param)
+    _check_out(out, mech.n_species + 1, ld, n, torch.float64, "out")
     if out is None:
         out = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
     work, wb = _workspace(mech, PJ_OP_SOURCE, n, phi.device)
@@ -302,6 +372,8 @@ def _dphi_like(mech, phi, ld, n):
 def jacobian_sparse(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=None, stream=None):
     import torch
     n, ld = _check_batch(mech, phi, param)
+    _check_out(out, mech.nnz, ld, n, torch.float64, "out")
+    _check_out(dphi, mech.n_species + 1, ld, n, torch.float64, "dphi")
     if out is None:
         out = torch.empty((mech.nnz, ld), dtype=torch.float64, device=phi.device)[:, :n]
     if dphi is None:
@@ -336,6 +408,8 @@ def jacobian_fd(mech, mode, phi, param, fmt=PJ_CSR, out=None, dphi=None, status=
     import torch
     n, ld = _check_batch(mech, phi, param)
     N1 = mech.n_species + 1
+    _check_out(out, N1 * N1 if fmt == PJ_DENSE else mech.nnz, ld, n, torch.float64, "out")
+    _check_out(dphi, N1, ld, n, torch.float64, "dphi")
     if out is None:
         rows = N1 * N1 if fmt == PJ_DENSE else mech.nnz
         out = torch.empty((rows, ld), dtype=torch.float64, device=phi.device)[:, :n]
@@ -350,6 +424,8 @@ def jacobian_dense(mech, mode, phi, param, out=None, dphi=None, status=None, str
     import torch
     n, ld = _check_batch(mech, phi, param)
     N1 = mech.n_species + 1
+    _check_out(out, N1 * N1, ld, n, torch.float64, "out")
+    _check_out(dphi, N1, ld, n, torch.float64, "dphi")
     if out is None:
         out = torch.empty((N1 * N1, ld), dtype=torch.float64, device=phi.device)[:, :n]
     if dphi is None:
@@ -366,6 +442,8 @@ def newton_matrix_f32(mech, mode, phi, param, h, gamma=1.0, fmt=PJ_CSR, out=None
     n, ld = _check_batch(mech, phi, param)
     N1 = mech.n_species + 1
     rows = N1 * N1 if fmt == PJ_DENSE else mech.nnz
+    _check_out(out, rows, ld, n, torch.float32, "out")
+    _check_out(dphi, N1, ld, n, torch.float64, "dphi")
     if out is None:
         out = torch.empty((rows, ld), dtype=torch.float32, device=phi.device)[:, :n]
     if dphi is None:
@@ -379,6 +457,7 @@ def eval_y(mech, mode, phi, param, out=None, status=None, stream=None):
     """y = (wdot_0 .. wdot_{Ns-1}, dT/dt), shape [Ns+1, n]."""
     import torch
     n, ld = _check_batch(mech, phi, param)
+    _check_out(out, mech.n_species + 1, ld, n, torch.float64, "out")
     if out is None:
         out = torch.empty((mech.n_species + 1, ld), dtype=torch.float64, device=phi.device)[:, :n]
     work, wb = _workspace(mech, PJ_OP_Y, n, phi.device)
@@ -413,15 +492,16 @@ def _make_function():
 
     class SourceTermsY(torch.autograd.Function):
         """y(phi, theta) = (wdot_0 .. wdot_{Ns-1}, dT/dt) with gradients by the
-        adjoint kernel.  theta [Nr, 3] must hold the mechanism's (ln A, beta,
-        Ea); it is the graph node for parameter sensitivities (the kernels
-        read the values packed in the mechanism)."""
+        adjoint kernel.  theta [Nr, 3] holds each reaction's high-pressure
+        (or only) (ln A, beta, Ea): where it differs from the handle's, the
+        evaluation and both gradients use a handle with theta's parameters
+        (pj_mech_with_arrhenius; the last one is kept for the next call)."""
 
         @staticmethod
         def forward(ctx, phi, theta, mech, mode, param):
-            ctx.mech, ctx.mode = mech, mode
+            ctx.mech, ctx.mode = _mech_at(mech, theta), mode
             ctx.save_for_backward(phi, param)
-            return eval_y(mech, mode, phi.detach(), param)
+            return eval_y(ctx.mech, mode, phi.detach(), param)
 
         @staticmethod
         def backward(ctx, gy):
@@ -438,6 +518,21 @@ def _make_function():
 
 
 _Y = None
+
+
+def _mech_at(mech, theta):
+    """mech itself when theta [Nr, 3] equals its (ln A, beta, Ea), else a
+    handle with theta's parameters (cached on mech for the last theta)."""
+    t = theta.detach().to("cpu", dtype=__import__("torch").float64).numpy().reshape(mech.n_reactions, 3)
+    if not hasattr(mech, "_theta0"):
+        mech._theta0 = np.stack(mech.arrhenius(), axis=1)
+        mech._theta_cache = (None, None)
+    if np.array_equal(t, mech._theta0):
+        return mech
+    key = t.tobytes()
+    if mech._theta_cache[0] != key:
+        mech._theta_cache = (key, mech.with_arrhenius(t[:, 0], t[:, 1], t[:, 2]))
+    return mech._theta_cache[1]
 
 
 def source_terms_y(mech, mode, phi, param, theta):

@@ -46,6 +46,55 @@ extern "C" int pj_workspace_size(const pj_mech* m, int op, int64_t n, size_t* by
   }
 }
 
+extern "C" int pj_debug_word(const pj_mech* m, uint32_t* h_word, int clear) {
+  if (!m || !h_word) return fail(PJ_ERR_ARG, "pj_debug_word: null argument");
+  if (m->device < 0 || !m->dm.dbg) return fail(PJ_ERR_CUDA, "pj_debug_word: mechanism has no device copy");
+  int rc;
+  if ((rc = check_cuda(cudaMemcpy(h_word, m->dm.dbg, sizeof(uint32_t), cudaMemcpyDeviceToHost),
+                       "cudaMemcpy(debug word)")))
+    return rc;
+  if (clear) return check_cuda(cudaMemset(m->dm.dbg, 0, sizeof(uint32_t)), "cudaMemset(debug word)");
+  return PJ_OK;
+}
+
+extern "C" int pj_debug_build(int32_t* on) {
+  if (!on) return fail(PJ_ERR_ARG, "pj_debug_build: null argument");
+#ifdef PJ_DEBUG_BOUNDS
+  *on = 1;
+#else
+  *on = 0;
+#endif
+  return PJ_OK;
+}
+
+extern "C" int pj_debug_set_target(const pj_mech* m, int fmt, int32_t index, int32_t value) {
+#ifdef PJ_DEBUG_BOUNDS
+  if (!m) return fail(PJ_ERR_ARG, "pj_debug_set_target: null mechanism");
+  if (fmt != PJ_CSR && fmt != PJ_CSC) return fail(PJ_ERR_ARG, "pj_debug_set_target: fmt must be PJ_CSR or PJ_CSC");
+  if (m->device < 0) return fail(PJ_ERR_CUDA, "pj_debug_set_target: mechanism has no device copy");
+  if (index < 0 || index >= m->dm.n_tgt) return fail(PJ_ERR_ARG, "pj_debug_set_target: index out of range");
+  int32_t* p = const_cast<int32_t*>(fmt == PJ_CSR ? m->dm.tgt_csr : m->dm.tgt_csc) + index;
+  return check_cuda(cudaMemcpy(p, &value, sizeof value, cudaMemcpyHostToDevice), "cudaMemcpy(target entry)");
+#else
+  (void)m;
+  (void)fmt;
+  (void)index;
+  (void)value;
+  return fail(PJ_ERR_UNSUPPORTED, "pj_debug_set_target: only in the bounds-checked build (PJ_DEBUG_BOUNDS)");
+#endif
+}
+
+extern "C" int pj_jacobian_layout(const pj_mech* m, int fmt, int prec, int64_t n, int32_t* layout) {
+  if (!m || !layout) return fail(PJ_ERR_ARG, "pj_jacobian_layout: null argument");
+  if (n < 0) return fail(PJ_ERR_ARG, "pj_jacobian_layout: n < 0");
+  if (fmt != PJ_CSR && fmt != PJ_CSC && fmt != PJ_DENSE)
+    return fail(PJ_ERR_ARG, "pj_jacobian_layout: fmt must be PJ_CSR, PJ_CSC or PJ_DENSE");
+  if (prec != PJ_F64 && prec != PJ_F32) return fail(PJ_ERR_ARG, "pj_jacobian_layout: prec must be PJ_F64 or PJ_F32");
+  if (m->device < 0) return fail(PJ_ERR_CUDA, "pj_jacobian_layout: mechanism has no device copy");
+  *layout = jacobian_layout(m->dm, fmt, prec == PJ_F32, n);
+  return PJ_OK;
+}
+
 extern "C" int pj_eval_source_terms(const pj_mech* m, int mode, int64_t n, const double* param, const double* phi,
                                     int64_t ld, double* dphi, int* status, void* work, size_t work_bytes,
                                     void* stream) {

@@ -505,7 +505,8 @@ int mech_build(pj_mech* m) {
   const size_t o_tab = align256(o_etab + 256 * sizeof(double));
   const size_t o_tcsr = align256(o_tab + tab.size() * sizeof(double));
   const size_t o_tcsc = align256(o_tcsr + tgt_csr.size() * sizeof(int32_t));
-  const size_t total = align256(o_tcsc + tgt_csc.size() * sizeof(int32_t));
+  const size_t o_dbg = align256(o_tcsc + tgt_csc.size() * sizeof(int32_t));
+  const size_t total = align256(o_dbg + sizeof(uint32_t));
   // 2^(j/256) in extended precision, rounded once to double
   double etab[256];
   for (int j = 0; j < 256; j++) etab[j] = (double)std::exp2((long double)j / 256.0L);
@@ -567,6 +568,10 @@ int mech_build(pj_mech* m) {
   dm.tgt_csc = reinterpret_cast<const int32_t*>(b + o_tcsc);
   dm.has_pdep = has_pdep ? 1 : 0;
   dm.nr_plain = nr_plain;
+  dm.n_eff = (int32_t)eff_sp.size();
+  dm.n_rows = (int32_t)rows.size();
+  dm.n_tgt = (int32_t)tgt_csr.size();
+  dm.dbg = reinterpret_cast<uint32_t*>(b + o_dbg);
   return lu_build(m);
 }
 
@@ -690,13 +695,11 @@ extern "C" int pj_mech_info(const pj_mech* m, int32_t* ns, int32_t* nr, int32_t*
   return PJ_OK;
 }
 
-extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech** out) {
-  if (!src || !out) return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: null argument");
-  *out = nullptr;
-  if (form != PJ_JAC_EXACT && form != PJ_JAC_APPROX)
-    return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: form must be PJ_JAC_EXACT or PJ_JAC_APPROX");
+// A new handle holding a copy of src's mechanism description (not yet
+// packed or uploaded); nullptr when host memory runs out.
+static pj_mech* copy_description(const pj_mech* src) {
   pj_mech* m = new (std::nothrow) pj_mech();
-  if (!m) return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
+  if (!m) return nullptr;
   try {
     m->ns = src->ns;
     m->nr = src->nr;
@@ -736,9 +739,14 @@ extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech*
     m->cheb_coef = src->cheb_coef;
   } catch (...) {
     delete m;
-    return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
+    return nullptr;
   }
-  m->jac_form = form;
+  m->jac_form = src->jac_form;
+  return m;
+}
+
+// Pack and upload a described handle; on failure release it.
+static int finish_handle(pj_mech* m, pj_mech** out) {
   int rc = mech_build(m);
   if (rc) {
     mech_release(m);
@@ -747,6 +755,44 @@ extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech*
   }
   *out = m;
   return PJ_OK;
+}
+
+extern "C" int pj_mech_with_jacobian_form(const pj_mech* src, int form, pj_mech** out) {
+  if (!src || !out) return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: null argument");
+  *out = nullptr;
+  if (form != PJ_JAC_EXACT && form != PJ_JAC_APPROX)
+    return fail(PJ_ERR_ARG, "pj_mech_with_jacobian_form: form must be PJ_JAC_EXACT or PJ_JAC_APPROX");
+  pj_mech* m = copy_description(src);
+  if (!m) return fail(PJ_ERR_NOMEM, "pj_mech_with_jacobian_form: out of host memory");
+  m->jac_form = form;
+  return finish_handle(m, out);
+}
+
+extern "C" int pj_mech_arrhenius(const pj_mech* m, double* h_lnA, double* h_beta, double* h_Ea) {
+  if (!m || !h_lnA || !h_beta || !h_Ea) return fail(PJ_ERR_ARG, "pj_mech_arrhenius: null argument");
+  for (int i = 0; i < m->nr; i++) {
+    h_lnA[i] = std::log(m->A[i]);
+    h_beta[i] = m->beta[i];
+    h_Ea[i] = m->Ea[i];
+  }
+  return PJ_OK;
+}
+
+extern "C" int pj_mech_with_arrhenius(const pj_mech* src, const double* h_lnA, const double* h_beta,
+                                      const double* h_Ea, pj_mech** out) {
+  if (!src || !h_lnA || !h_beta || !h_Ea || !out) return fail(PJ_ERR_ARG, "pj_mech_with_arrhenius: null argument");
+  *out = nullptr;
+  for (int i = 0; i < src->nr; i++)
+    if (!std::isfinite(h_lnA[i]) || !std::isfinite(h_beta[i]) || !std::isfinite(h_Ea[i]))
+      return fail(PJ_ERR_ARG, "pj_mech_with_arrhenius: non-finite parameter of reaction " + std::to_string(i));
+  pj_mech* m = copy_description(src);
+  if (!m) return fail(PJ_ERR_NOMEM, "pj_mech_with_arrhenius: out of host memory");
+  for (int i = 0; i < m->nr; i++) {
+    m->A[i] = std::exp(h_lnA[i]);
+    m->beta[i] = h_beta[i];
+    m->Ea[i] = h_Ea[i];
+  }
+  return finish_handle(m, out);
 }
 
 extern "C" int pj_mech_jacobian_form(const pj_mech* m, int32_t* form) {

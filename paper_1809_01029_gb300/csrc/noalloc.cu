@@ -11,7 +11,6 @@
 // nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "launch.h"
@@ -21,26 +20,18 @@
 namespace {
 
 constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB per device
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchBytes / sizeof(double)];
 
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on device `dev` (which must be
-// current).  Looked up once per device; the host-side symbol is only a
-// stand-in and must never be passed to a kernel.
-int scratch_address(int dev, double** out) {
-  if (dev < 0 || dev >= kMaxDevices) return pj::fail(PJ_ERR_UNSUPPORTED, "pj_eval_jacobian_sparse_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return pj::check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+// Device address of the scratch array in the current device's context.  The
+// host-side symbol is only a stand-in and must never be passed to a kernel.
+// Looked up on every call (the lookup does not allocate): a cached address
+// would go stale if the context were reset and the module loaded again.
+int scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return pj::check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
+  *out = static_cast<double*>(p);
   return PJ_OK;
 }
 
@@ -63,11 +54,8 @@ extern "C" int pj_eval_jacobian_sparse_noalloc(const pj_mech* m, int mode, int f
     return fail(PJ_ERR_UNSUPPORTED, std::string(fn) + ": mechanism too large for the fixed scratch (" +
                                         std::to_string(per_thread * 128) + " bytes needed per 128 states, " +
                                         std::to_string(kScratchBytes) + " bytes available)");
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return check_cuda(e, "cudaGetDevice");
   double* scratch = nullptr;
-  if ((rc = scratch_address(dev, &scratch))) return rc;
+  if ((rc = scratch_address(&scratch))) return rc;
   return launch_jacobian_on_scratch(m->dm, mode, fmt, n, param, phi, ld, vals, dphi, status, scratch, threads,
                                     (cudaStream_t)stream);
 }

@@ -198,3 +198,28 @@ def test_lu_ordering_and_pattern_874_species(lib, mechs):
     k, p = h.lu_info()
     hr, hc = h.lu_pattern()
     assert k == len(r) and np.array_equal(p, perm) and np.array_equal(hr, r) and np.array_equal(hc, c)
+
+
+def test_arrhenius_parameters_round_trip(lib, mechs):
+    """pj_mech_arrhenius returns (ln A, beta, Ea) in reaction order;
+    pj_mech_with_arrhenius makes a new handle with them replaced and leaves
+    the source handle as it was; non-finite parameters are rejected."""
+    m = mechs("gri53_types")
+    h = pj.pj_mech_create(m)
+    a, b, e = h.arrhenius()
+    assert np.array_equal(a, np.log(m.A)) and np.array_equal(b, m.beta) and np.array_equal(e, m.Ea)
+    rng = np.random.default_rng(5)
+    a2, b2, e2 = a + rng.normal(0, 0.1, a.shape), b + 0.05, e * 1.01
+    h2 = pj.pj_mech_with_arrhenius(h, a2, b2, e2)
+    got = h2.arrhenius()
+    assert np.allclose(got[0], a2, rtol=0, atol=4e-15 * np.abs(a2).max()) and np.array_equal(got[1], b2)
+    assert np.array_equal(got[2], e2)
+    assert np.array_equal(h.arrhenius()[0], a)
+    assert h2.nnz == h.nnz and h2.jacobian_form == h.jacobian_form
+    bad = a2.copy()
+    bad[3] = np.nan
+    with pytest.raises(pj.PJError) as err:
+        h.with_arrhenius(bad, b2, e2)
+    assert err.value.code == N.PJ_ERR_ARG
+    with pytest.raises(ValueError):
+        h.with_arrhenius(a2[:-1], b2, e2)

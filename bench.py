@@ -35,80 +35,110 @@ METRIC = "Jacobian & source-term evals/s (states/s) at FP64 tol vs oracle; roofl
 UNIT = "states/s"
 WORKLOAD = "gri53_1m"
 
-# FP64 cost of an exp / log / divide in DFMA-equivalents: the kernels' exp is
-# the table-driven one (9 FP64 operations: reduction 3, polynomial 4, table
-# product 1, shift 1); log and divide are CUDA's, measured on this GB300 in
-# DFMA issue slots (dfma 505 G/s, log 16.7 G/s, div 88.9 G/s).
-W_EXP, W_LOG, W_DIV = 9.0, 30.2, 5.7
 # FP64 peak derived from unit counts and clock: 2 DFMA / clock / SM
 # (1.25 TFLOP/s nominal for GB300) x 152 SMs x 2070 MHz.
 FP64_DFMA_PER_CLK_SM = 2.0
+# FP32 FMA issue rate relative to FP64 on this part (128 vs 2 per clock per SM)
+FP32_PER_FP64 = 64.0
 
 
 CPU_SAMPLE = 4096   # states of the oracle's timed sample (10-30 s of one core)
 
+# Algorithmic work per state: the operation counts of the oracle's formulas
+# (a counting scalar run through the source terms, and forward-mode through
+# their derivatives, by oracle/opcount.py), stored with their weights in
+# oracle/work_counts.json by `python -m oracle.opcount` (the timed legs read
+# the table and run no oracle code).
+WORK_TABLE = os.path.join(ROOT, "oracle", "work_counts.json")
+_WORK = None
 
-def fp64_work_per_state(m, jacobian=True):
-    """Algorithmic FP64 work per state in DFMA-equivalents: every add, multiply
-    and FMA of the formulas counts 1, exp 9 (the FP64 operations of the
-    table-driven exp), log 30.2 and divide 5.7 (CUDA's routines on this part,
-    in DFMA issue slots).
-    The Jacobian's entry accumulations run as L2 reductions and are not
-    counted."""
-    import synth
-    ns, nr = m.n_species, m.n_reactions
-    w = 0.0
-    w += (ns - 1) * W_DIV + (ns - 1) + 3 + W_DIV       # concentrations, C_tot, bath gas
-    w += W_LOG + W_DIV + 15 * ns + ns                   # ln T, 1/T, NASA-7 cp/h/s/g, denominator
-    for i in range(nr):
-        r, p = m.reactants(i), m.products(i)
-        nre, npr = len(r), len(p)
-        sre, spr = sum(v for _, v in r), sum(v for _, v in p)
-        kind = int(m.kind[i])
-        w += 2 + W_EXP + (sre - 1) + 1                  # kf and forward product
-        if kind == synth.PLOG:                          # segment search, two ln k, interpolation
-            w += int(m.plog_ptr[i + 1] - m.plog_ptr[i]) + 2 * 2 + 3
-        elif kind == synth.CHEB:                        # reduced T and P, recurrences, double sum
-            nT, nP = (int(x) for x in m.cheb_shape[i])
-            w += 4 + 2 * (nT + nP) + nT * nP + nT
-        if m.reversible[i] and m.rev_explicit[i]:
-            w += 2 + W_EXP + (spr - 1) + 1              # explicit reverse Arrhenius
-        elif m.reversible[i]:
-            w += (nre + npr) + 2 + W_EXP + (spr - 1) + 1
-        if kind != synth.ELEMENTARY:
-            w += len(m.efficiencies(i))
-        if kind in (synth.LINDEMANN, synth.TROE, synth.SRI):
-            w += 2 + W_EXP + 1 + W_DIV + 2             # k0/kinf, Pr, Pr/(1+Pr) F
-            if kind == synth.TROE:
-                w += (3 if m.troe_n[i] == 4 else 2) * W_EXP + 2 * W_LOG + W_EXP + W_DIV * 2 + 12
-            elif kind == synth.SRI:
-                w += 3 * W_EXP + 2 * W_LOG + W_DIV + 8
-        w += 2 + (nre + npr)                            # q, production-rate scatter
-        if jacobian:
-            w += 2 + nre + (nre + npr)                  # dln kf/dT, dRf/dC, sum nu h
-            if m.reversible[i]:
-                w += 3 + npr
-            if kind == synth.PLOG:
-                w += 6
-            elif kind == synth.CHEB:
-                nT, nP = (int(x) for x in m.cheb_shape[i])
-                w += 2 * (nT + nP) + nT * nP + nT + 2
-            if kind == synth.THIRD_BODY:
-                w += 4
-            elif kind in (synth.LINDEMANN, synth.TROE, synth.SRI):
-                w += 2 + 12 + W_DIV
-                if kind == synth.TROE:
-                    w += 16 + W_DIV
-                elif kind == synth.SRI:
-                    w += 10 + W_DIV
-            w += 4 + (nre + npr) + 4 + 3 + 4          # dR/dT, dR/dS, dq/dT, dq/dS, dE, accumulators
-            rows = sum(1 for k in range(ns - 1) if (sum(v for kk, v in p if kk == k) - sum(v for kk, v in r if kk == k)) != 0)
-            slots = nre + (npr if m.reversible[i] else 0) + (len(m.efficiencies(i)) if kind != synth.ELEMENTARY else 0)
-            w += 2 * rows + slots * (1 + rows + 2)     # products feeding the L2 reductions
-    w += ns + 2 * (ns - 1) + W_DIV + 10                 # energy and state equations
-    if jacobian:
-        w += (ns + 1) * (12 + 2 * W_DIV) + 2 * ns + 4 * W_DIV   # T and S rows
-    return w
+
+def work_table():
+    global _WORK
+    if _WORK is None:
+        with open(WORK_TABLE) as f:
+            _WORK = json.load(f)
+    return _WORK
+
+
+def dfma_equiv(counts, weights):
+    """FP64 work in DFMA-equivalents; entry accumulations ("acc") are L2
+    reductions in the kernels, off the FP64 pipe, and are not counted."""
+    return sum(weights[c] * counts[c] for c in counts if c != "acc")
+
+
+def work_per_state(mech_name, op, mode="conp"):
+    """(DFMA-equivalent FP64 work per state, the counts) of one evaluation:
+    source terms; the Jacobian (source terms and forward-mode derivatives);
+    the FP32 Newton matrix (the derivative part in FP32, at 1/64 of an FP64
+    operation); the VJP (the derivatives of y, as the Jacobian's); the LU
+    factorisation of the Newton matrix ("lu"), and with M = I - h gamma J
+    formed from the Jacobian's values first ("newton_lu", what the factor
+    kernel does when given J and h)."""
+    t = work_table()
+    w, c = t["weights"], t["counts"][mech_name]
+    if op == "source":
+        k = c[f"source_{mode}"]
+        return dfma_equiv(k, w), k
+    if op in ("lu", "newton_lu"):
+        return dfma_equiv(c[op], w), c[op]
+    k = c[f"jacobian_{mode}"]
+    full = dfma_equiv(k, w)
+    if op == "newton":
+        src = dfma_equiv(c[f"source_{mode}"], w)
+        return src + (full - src) / FP32_PER_FP64, k
+    return full, k
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the fallback measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(op, ns, h):
+    """Bytes one state's evaluation must move to or from HBM (8-byte values;
+    the mechanism's constants are shared by all states and not counted):
+    state Phi (Ns+1) and parameter in, outputs out."""
+    N = ns + 1
+    io = (N + 1) * 8
+    if op == "source":
+        return io + N * 8
+    if op in ("jac_csr", "jac_csc"):
+        return io + (h.nnz + N) * 8
+    if op == "jac_dense":
+        return io + (N * N + N) * 8
+    if op == "newton":
+        return io + 8 + h.nnz * 4 + N * 8
+    if op == "vjp":
+        return io + N * 8 + 2 * N * 8           # cotangents in; y and g_Phi out
+    if op == "lu":
+        return h.nnz * 8 + 8 + h.lu_info()[0] * 8
+    return None
+
+
+def t_roof(work, nbytes, n, ms, peak_g, weights):
+    """The roofline time of the step, t_roof = max(bytes / HBM peak, sum over
+    operation classes of ops_c / peak_c), each class's peak the FP64 pipe's
+    DFMA rate divided by its cost in DFMA issue slots, and the fraction
+    t_roof / t_measured."""
+    hbm, src = hbm_peak_gbs()
+    t_hbm = nbytes * n / (hbm * 1e9) * 1e3 if nbytes else 0.0
+    t_fp64 = work * n / (peak_g * 1e9) * 1e3
+    tr = max(t_hbm, t_fp64)
+    return {"ms": tr, "frac": tr / ms, "hbm_ms": t_hbm, "fp64_ms": t_fp64, "bytes_per_state": nbytes,
+            "hbm_gbs": hbm, "hbm_source": src,
+            "class_peaks_g_per_s": {c: peak_g / weights[c] for c in weights if c != "acc"}}
+
+
+def class_shares(counts, weights):
+    """Share of each operation class in the FP64-pipe time of the count."""
+    tot = dfma_equiv(counts, weights)
+    return {cls: weights[cls] * v / tot for cls, v in counts.items() if cls != "acc" and v}
 
 
 def sample_clocks_start(path):
@@ -198,6 +228,105 @@ def oracle_baseline_parallel(m, mode, per_proc, seed, procs):
     return done / dt, dt
 
 
+# The other workloads' oracle timing (--cpu-configs): each on a bounded
+# sample, one core and every core.  (mechanism, what, states per process,
+# Jacobian columns timed: None = all)
+CPU_CONFIGS = [("h2co13", "source + CSR Jacobian", 2048, None),
+               ("gri53", "source + CSR Jacobian", 512, None),
+               ("usc111", "source + FP64 Newton matrix", 64, None),
+               ("gri53", "VJP", 256, None),
+               ("ic5874", "source + CSR Jacobian", 4, 16)]
+
+
+def _oracle_config_work(job):
+    """One process's share of a configuration's oracle timing: the seconds
+    for its states (for the 874-species Jacobian, `cols` of the 875 columns
+    timed and the time scaled to all of them)."""
+    import oracle
+    m, what, phi, par, cols = job
+    t0 = time.perf_counter()
+    if what == "VJP":
+        import synth
+        uw, uT = synth.make_cotangents(m.n_species, phi.shape[1], 5)
+        oracle.vjp(m, 0, phi, par, uw, uT)
+    else:
+        oracle.source_terms(m, 0, phi, par)
+        if cols is None:
+            J = oracle.jacobian(m, 0, phi, par)
+            if what.endswith("Newton matrix"):
+                N1 = m.n_species + 1
+                J = -1e-7 * J
+                J[np.arange(N1), np.arange(N1)] += 1.0
+            oracle.dense_to_csr_values(m, J)
+        else:
+            t1 = time.perf_counter()
+            oracle.jacobian_columns(m, 0, phi, par, list(range(cols)))
+            return (t1 - t0) + (time.perf_counter() - t1) * (m.n_species + 1) / cols
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_configs(procs):
+    """States/s of the oracle on every configuration's workload, on one core
+    and on `procs` spawned processes (bounded samples)."""
+    import multiprocessing as mp
+    import synth
+    out = []
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_import, range(procs), chunksize=1)
+        for name, what, per, cols in CPU_CONFIGS:
+            m = synth.make_mechanism(name)
+            phi, par = synth.make_states(m, per * procs, 2018 + 9, synth.CONP)
+            dt1 = _oracle_config_work((m, what, phi[:, :per], par[:per], cols))
+            jobs = [(m, what, np.ascontiguousarray(phi[:, i * per:(i + 1) * per]),
+                     np.ascontiguousarray(par[i * per:(i + 1) * per]), cols) for i in range(procs)]
+            t0 = time.perf_counter()
+            secs = pool.map(_oracle_config_work, jobs, chunksize=1)
+            dta = time.perf_counter() - t0 if cols is None else max(secs)
+            out.append({"mechanism": name, "what": what, "one_core_states_per_s": per / dt1,
+                        "all_cores_states_per_s": per * procs / dta, "cores": procs,
+                        "sample_states_per_process": per,
+                        "note": None if cols is None else f"Jacobian time scaled from {cols} of the "
+                                                          f"{m.n_species + 1} columns"})
+    return out
+
+
+def batch_sweep(pj, synth, torch, dev, stream):
+    """States/s against batch size (the GB300 counterpart of Sec. 3.5.1's
+    GPU saturation study): source terms and source terms + CSR Jacobian of
+    the 53/325 mechanism, one launch each, 1 ki .. 1 Mi states."""
+    m = synth.make_mechanism("gri53")
+    h = pj.pj_mech_create(m)
+    N1 = m.n_species + 1
+    nmax = 1 << 20
+    phi_h, par_h = synth.make_states(m, nmax, 2018 + 2, synth.CONP)
+    phi, par = torch.from_numpy(phi_h).to(dev), torch.from_numpy(par_h).to(dev)
+    del phi_h, par_h
+    f = torch.empty((N1, nmax), dtype=torch.float64, device=dev)
+    J = torch.empty((h.nnz, nmax), dtype=torch.float64, device=dev)
+    out = {}
+    for lg in range(10, 21, 2):
+        n = 1 << lg
+        ws = h.workspace_size(pj.PJ_OP_SOURCE, n)
+        w = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+        reps = max(3, min(200, (1 << 22) // n))
+        ts = _time(torch, stream, lambda: pj.pj_eval_source_terms(h, synth.CONP, n, par, phi, nmax, f, None, w, ws,
+                                                                  stream), reps=reps)
+        wj = h.workspace_size(pj.PJ_OP_JACOBIAN, n)
+        w2 = torch.empty(max(wj, 1), dtype=torch.uint8, device=dev)
+        tj = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, nmax, J,
+                                                                     f, None, w2, wj, stream),
+                   reps=max(3, reps // 3))
+        out[str(n)] = {"source": n / (ts * 1e-3), "jacobian_csr": n / (tj * 1e-3)}
+    del J, f, phi, par
+    torch.cuda.empty_cache()
+    return out
+
+
+def fp64_peak(torch, dev, sm_mhz=2070.0):
+    """Derived FP64 peak, DFMA per second: 2 per clock per SM x SMs x clock."""
+    return FP64_DFMA_PER_CLK_SM * torch.cuda.get_device_properties(dev).multi_processor_count * sm_mhz * 1e6
+
+
 def _time(torch, stream, fn, reps=5):
     fn()
     torch.cuda.synchronize()
@@ -211,22 +340,14 @@ def _time(torch, stream, fn, reps=5):
     return a.elapsed_time(b) / reps
 
 
-def lu_work_per_state(h):
-    """FP64 work of one LU factorisation in DFMA-equivalents: for pivot k,
-    |rows| x |cols| fused multiply-adds and |rows| multiplies, and one
-    divide (rows/cols: the fill pattern's column below and row right of k)."""
-    r, c = h.lu_pattern()
-    N = h.n_species + 1
-    rows = np.bincount(c[r > c], minlength=N)
-    cols = np.bincount(r[c > r], minlength=N)
-    return float(np.sum(rows * cols) + np.sum(rows) + N * W_DIV)
-
-
-# ncu DRAM bytes per state of a kernel, recorded in profiles/ together with a
-# hash of the kernel sources at capture time; a number is only used while
-# the sources are unchanged.
-PROFILE_OF = {("jac_csr", "gri53"): "k_jacobian_tm_gri53.md", ("source", "gri53"): "k_source_terms_gri53.md",
-              ("lu", "gri53"): "k_lu_factor_gri53.md"}
+# Per-state ncu figures of a kernel (DRAM bytes, executed FP64-pipe
+# instructions), recorded in profiles/ together with a hash of the kernel
+# sources at capture time; a number is only used while the sources are
+# unchanged.
+PROFILE_OF = {("k_jacobian_coop", "gri53"): "k_jacobian_coop_gri53.md",
+              ("k_jacobian_tm", "gri53"): "k_jacobian_tm_gri53.md",
+              ("k_source_terms", "gri53"): "k_source_terms_gri53.md",
+              ("k_lu_factor_v", "gri53"): "k_lu_factor_gri53.md"}
 
 
 def sources_hash():
@@ -241,18 +362,28 @@ def sources_hash():
     return d.hexdigest()[:16]
 
 
-def kernel_traffic(op, mech_name):
-    name = PROFILE_OF.get((op, mech_name))
+def _profile_figure(kern, mech_name, key):
+    name = PROFILE_OF.get((kern, mech_name))
     if not name:
         return None
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     import re
-    m = re.search(r"traffic_bytes_per_state:\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]+)", open(path).read())
+    m = re.search(key + r":\s*([0-9.eE+]+)\s+sources:\s*([0-9a-f]+)", open(path).read())
     if not m or m.group(2) != sources_hash():
         return None
     return float(m.group(1))
+
+
+def kernel_traffic(op, mech_name, kern):
+    """DRAM bytes per state of the kernel's profile (None once stale)."""
+    return _profile_figure(kern, mech_name, "traffic_bytes_per_state")
+
+
+def kernel_executed(op, mech_name, kern):
+    """Executed FP64-pipe instructions per state of the kernel's profile."""
+    return _profile_figure(kern, mech_name, "fp64_pipe_instr_per_state")
 
 
 def lu_workloads(pj, synth, torch, dev, stream):
@@ -292,7 +423,12 @@ def lu_workloads(pj, synth, torch, dev, stream):
                   reps=reps)
         tag = f"{name}_256k_lu_{'f64' if prec == pj.PJ_F64 else 'f32'}"
         out[f"{tag}_factor"] = n / (t * 1e-3)
+        if prec == pj.PJ_F64:
+            out[f"{tag}_factor_fp64_frac"] = (work_per_state(name, "newton_lu")[0] * n / (t * 1e-3) /
+                                              fp64_peak(torch, dev))
         out[f"{tag}_states_flagged"] = int(status.item()) // (reps + 1)
+        if prec == pj.PJ_F32:
+            out[f"{tag}_flagged_states"] = lu_nonfinite_states(torch, h, vals, lu, hs)
         b = torch.randn((N1, n), dtype=dt, device=dev)
         x = torch.empty_like(b)
         t = _time(torch, stream, lambda: pj.pj_lu_solve(h, prec, n, lu, n, b, x, stream), reps=10)
@@ -330,12 +466,15 @@ def other_workloads(pj, synth, torch, dev, stream):
     t = _time(torch, stream, lambda: pj.pj_newton_matrix_f32(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, hs, 1.0, M, f,
                                                              None, w, wb, stream), reps=3)
     out["usc111_256k_newton_f32_csr"] = n / (t * 1e-3)
-    del M
+    peak = fp64_peak(torch, dev)
+    out["usc111_256k_newton_f32_csr_fp64_frac"] = work_per_state("usc111", "newton")[0] * n / (t * 1e-3) / peak
     J = torch.empty((h.nnz, n), dtype=torch.float64, device=dev)
     t = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f, None,
                                                                 w, wb, stream), reps=3)
     out["usc111_256k_jacobian_f64_csr"] = n / (t * 1e-3)
-    del J, w
+    out["usc111_256k_jacobian_f64_csr_fp64_frac"] = work_per_state("usc111", "jacobian")[0] * n / (t * 1e-3) / peak
+    out["usc111_256k_newton_f32_error"] = newton_f32_error(torch, h, M, J, hs)
+    del M, J, w
     # 53 species / 325 reactions, 65,536 states: adjoint VJP
     m = synth.make_mechanism("gri53")
     h = pj.pj_mech_create(m)
@@ -352,6 +491,7 @@ def other_workloads(pj, synth, torch, dev, stream):
     t = _time(torch, stream, lambda: pj.pj_vjp(h, synth.CONP, n, par, phi, n, uw, uT, y, g, gt, None, w, wb, stream),
               reps=10)
     out["gri53_64k_vjp"] = n / (t * 1e-3)
+    out["gri53_64k_vjp_fp64_frac"] = work_per_state("gri53", "vjp")[0] * n / (t * 1e-3) / peak
     del y, g, gt, w, uw, uT
     # same states: analytical vs first-order finite-difference CSR Jacobian
     # (the paper's speedup comparison)
@@ -361,6 +501,10 @@ def other_workloads(pj, synth, torch, dev, stream):
     w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
     ta = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f,
                                                                  None, w, wb, stream), reps=10)
+    out["gri53_64k_jacobian_csr"] = n / (ta * 1e-3)
+    tn = _time(torch, stream, lambda: pj.pj_eval_jacobian_sparse_noalloc(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J,
+                                                                         f, None, stream), reps=10)
+    out["gri53_64k_jacobian_csr_noalloc"] = n / (tn * 1e-3)
     wb = h.workspace_size(pj.PJ_OP_FD, n)
     w = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
     tf = _time(torch, stream, lambda: pj.pj_eval_jacobian_fd(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, J, f,
@@ -369,10 +513,63 @@ def other_workloads(pj, synth, torch, dev, stream):
     out["gri53_64k_analytical_over_fd"] = tf / ta
     del J, f, w, phi, par
     torch.cuda.empty_cache()
+    out["gri53_batch_sweep"] = batch_sweep(pj, synth, torch, dev, stream)
     out.update(types_workload(pj, synth, torch, dev, stream))
     out.update(lu_workloads(pj, synth, torch, dev, stream))
     out.update(ragged_workload(pj, synth, torch, dev, stream))
     return out
+
+
+def newton_f32_error(torch, h, M, J, hs, gamma=1.0, chunk=16384):
+    """Error of the FP32 Newton matrix M against M64 = I - h gamma J formed
+    in FP64 from the FP64 Jacobian of the same states (itself held to the
+    oracle by the parity tests), over every state of the batch: per state
+    ||M - M64||_F / ||M64||_F, and per entry |M - M64| / max_ij |M64| of
+    its state; plus how many states have a non-finite FP32 entry."""
+    ptr, idx = h.sparsity()
+    rows = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+    diag = torch.from_numpy(np.nonzero(rows == idx)[0]).to(M.device)
+    n = M.shape[1]
+    frob, ent, nonfinite = [], [], 0
+    for s0 in range(0, n, chunk):
+        s1 = min(n, s0 + chunk)
+        M64 = -(gamma * hs[s0:s1])[None, :] * J[:, s0:s1]
+        M64[diag] += 1.0
+        d = M[:, s0:s1].double() - M64
+        ok = torch.isfinite(d).all(0)
+        nonfinite += int((~ok).sum())
+        d, M64 = d[:, ok], M64[:, ok]
+        frob.append(torch.linalg.vector_norm(d, dim=0) / torch.linalg.vector_norm(M64, dim=0))
+        ent.append(d.abs().amax(0) / M64.abs().amax(0))
+    frob, ent = torch.cat(frob), torch.cat(ent)
+    q = lambda x, p: float(torch.quantile(x.float().cpu(), p))
+    return {"against": "M64 = I - h gamma J from the FP64 Jacobian of the same states, every state",
+            "frobenius_rel": {"median": q(frob, 0.5), "p99": q(frob, 0.99), "max": float(frob.max())},
+            "max_entry_rel_to_state_max": {"median": q(ent, 0.5), "p99": q(ent, 0.99), "max": float(ent.max())},
+            "nonfinite_states": nonfinite}
+
+
+def lu_nonfinite_states(torch, h, vals, lu, hs):
+    """Which states the FP32 LU flags, and where: how many; the median of
+    max |M| over flagged and over finite states; the pivot step (min(row,
+    col) of the first non-finite factor value in storage order) histogram;
+    and how many flagged states had a non-finite M to begin with."""
+    bad = ~torch.isfinite(lu).all(0)
+    k = int(bad.sum())
+    if k == 0:
+        return {"states": 0}
+    amax = vals.abs().amax(0).double()
+    Mbad = ~torch.isfinite(vals).all(0)
+    rows, cols = h.lu_pattern()
+    piv = torch.from_numpy(np.minimum(rows, cols)).to(lu.device)
+    first = (~torch.isfinite(lu[:, bad])).int().argmax(0)
+    steps, counts = torch.unique(piv[first], return_counts=True)
+    order = torch.argsort(counts, descending=True)[:8]
+    return {"states": k, "of": int(lu.shape[1]), "with_nonfinite_M": int((Mbad & bad).sum()),
+            "max_abs_M_median_flagged": float(amax[bad & ~Mbad].median()) if int((bad & ~Mbad).sum()) else None,
+            "max_abs_M_median_finite": float(amax[~bad].median()),
+            "h_median_flagged": float(hs[bad].median()), "h_median_finite": float(hs[~bad].median()),
+            "first_nonfinite_pivot_step": {int(steps[i]): int(counts[i]) for i in order}}
 
 
 def types_workload(pj, synth, torch, dev, stream):
@@ -397,12 +594,11 @@ def types_workload(pj, synth, torch, dev, stream):
     ts = _time(torch, stream, lambda: pj.pj_eval_source_terms(h, synth.CONP, n, par, phi, n, f, status, w2, ws,
                                                               stream), reps=5)
     assert int(status.item()) == 0
-    props = torch.cuda.get_device_properties(dev)
-    peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * 2070.0e6
+    peak = fp64_peak(torch, dev)
     out = {"gri53types_1m_jacobian_csr": n / (t * 1e-3),
-           "gri53types_1m_jacobian_csr_fp64_frac": fp64_work_per_state(m) * n / (t * 1e-3) / peak,
+           "gri53types_1m_jacobian_csr_fp64_frac": work_per_state("gri53_types", "jacobian")[0] * n / (t * 1e-3) / peak,
            "gri53types_1m_source": n / (ts * 1e-3),
-           "gri53types_1m_source_fp64_frac": fp64_work_per_state(m, jacobian=False) * n / (ts * 1e-3) / peak}
+           "gri53types_1m_source_fp64_frac": work_per_state("gri53_types", "source")[0] * n / (ts * 1e-3) / peak}
     del J, f, w, w2, phi, par
     torch.cuda.empty_cache()
     return out
@@ -470,6 +666,8 @@ def ragged_workload(pj, synth, torch, dev, stream):
     assert int(r["status"].item()) == 0
     total = r["total"]
     res = {"ic5874_ragged_jacobian_csr_graph": total / (t * 1e-3),
+           "ic5874_ragged_jacobian_csr_graph_fp64_frac":
+               work_per_state("ic5874", "jacobian")[0] * total / (t * 1e-3) / fp64_peak(torch, dev),
            "ic5874_ragged_info": {"batches": len(r["sizes"]), "states": total, "groups": len(r["groups"]),
                                   "config": plan.config(), "ms_per_replay": t}}
     del plan, r
@@ -534,15 +732,16 @@ def run_ragged(args, rank, world, local, torch, dist, synth, pj):
         dist.barrier()
     ms_max = replicas.max_over_ranks(ms, dist if world > 1 else None)
     assert int(r["status"].item()) == 0, "invalid states in the benchmark batches"
-    fp64_work = fp64_work_per_state(m)
+    fp64_work, counts = work_per_state("ic5874", "jacobian")
     achieved = fp64_work * n / (ms * 1e-3) / 1e9
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
                 "frac": achieved / peak, "traffic": None, "kernel": "k_batched", "work_per_state": fp64_work,
+                "work_source": "oracle operation count (oracle/work_counts.json)", "counts": counts,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
-    tr = kernel_traffic("ragged", "ic5874")
+    tr = kernel_traffic("ragged", "ic5874", "k_batched")
     if tr is not None:
         roofline["traffic"] = tr * n
         roofline["traffic_source"] = "ncu dram bytes per state of the current kernel sources x states"
@@ -573,6 +772,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="also time the oracle on every configuration's workload (bounded samples, one and all cores)")
     ap.add_argument("--clocks-dir", default=None, help="where to keep the nvidia-smi clock samples (default: a temp dir)")
     ap.add_argument("--op", default="jac_csr",
                     choices=["jac_csr", "jac_csc", "jac_dense", "source", "newton", "vjp", "lu", "ragged"],
@@ -682,21 +883,33 @@ def main():
     value = n * world / (ms_max * 1e-3)
     assert int(status.item()) == 0, "invalid states in the benchmark batch"
 
-    # roofline of the (single) kernel of the step: FP64 pipe
-    if args.op == "lu":
-        fp64_work = lu_work_per_state(h)
-    else:
-        fp64_work = fp64_work_per_state(m, jacobian=args.op not in ("source",))
+    # roofline of the (single) kernel of the step: FP64 pipe, against the
+    # method's operation count (oracle table) and, beside it, the FP64-pipe
+    # instructions the kernel executed (ncu, recorded in profiles/)
+    wop = {"jac_csr": "jacobian", "jac_csc": "jacobian", "jac_dense": "jacobian", "lu": "newton_lu"}.get(args.op,
+                                                                                                        args.op)
+    fp64_work, counts = work_per_state(mech_name, wop, args.mode)
     achieved = fp64_work * n / (ms * 1e-3) / 1e9     # G DFMA-equivalent / s
-    props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
+    peak = fp64_peak(torch, dev, sm_max) / 1e9
+    weights = work_table()["weights"]
+    kern = {"source": "k_source_terms", "vjp": "k_vjp", "lu": "k_lu_factor_v"}.get(args.op) or \
+        {0: "k_jacobian", 1: "k_jacobian_tm", 2: "k_jacobian_coop"}[h.jacobian_layout(
+            pj.PJ_DENSE if args.op == "jac_dense" else pj.PJ_CSR, pj.PJ_F32 if args.op == "newton" else pj.PJ_F64, n)]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": {"source": "k_source_terms", "vjp": "k_vjp", "lu": "k_lu_factor"}.get(args.op, "k_jacobian"),
+                "frac": achieved / peak, "traffic": None, "kernel": kern,
                 "work_per_state": fp64_work,
+                "work_source": "oracle operation count (oracle/work_counts.json, oracle/opcount.py): add, mul, "
+                               "fma 1, exp 9, log 30.2, div 5.7 DFMA-equivalents; entry accumulations (L2 "
+                               "reductions) not counted",
+                "counts": counts, "class_shares": class_shares(counts, weights),
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
-    tr = kernel_traffic(args.op, mech_name)
+    roofline["t_roof"] = t_roof(fp64_work, algorithmic_bytes(args.op, m.n_species, h), n, ms, peak, weights)
+    ex = kernel_executed(args.op, mech_name, kern)
+    if ex is not None:
+        roofline["executed"] = {"fp64_pipe_instr_per_state": ex, "frac": ex * n / (ms * 1e-3) / 1e9 / peak,
+                                "source": "ncu sm__inst_executed_pipe_fp64 x 32 per state of the current sources"}
+    tr = kernel_traffic(args.op, mech_name, kern)
     if tr is not None:
         roofline["traffic"] = tr * n
         roofline["traffic_source"] = "ncu dram bytes per state of the current kernel sources x states"
@@ -818,6 +1031,8 @@ def main():
                                      f"({dta:.1f} s)"}
             except Exception as e:  # noqa: BLE001 -- the figure is context only
                 cpu_all = {"unavailable": str(e)[:200]}
+        if args.cpu_configs:
+            variants["cpu_baseline_configs"] = cpu_baseline_configs(max(1, min(os.cpu_count() or 1, 64)))
 
     if rank == 0:
         print(json.dumps({

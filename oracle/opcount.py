@@ -366,8 +366,21 @@ def lu_counts(mech):
     return dict(add=0, mul=mul, fma=fma, div=N, exp=0, log=0, acc=0)
 
 
+def newton_lu_counts(mech):
+    """The LU of M = I - h gamma J formed from the Jacobian's values
+    (oracle.forms.newton_matrix, evaluated over the Jacobian's pattern): one
+    multiply per stored Jacobian entry and one add per diagonal entry, then
+    the factorisation of lu_counts."""
+    from .kinetics import sparsity_pattern
+    c = dict(lu_counts(mech))
+    c["mul"] += int(sparsity_pattern(mech).sum())
+    c["add"] += mech.n_species + 1
+    return c
+
+
 def build_table(names=TABLE_MECHS):
-    """{mechanism: {"source": counts, "jacobian": counts, "lu": counts}},
+    """{mechanism: {"source": counts, "jacobian": counts, "lu": counts,
+    "newton_lu": counts}},
     counts per state (mean of the states of per_state) in CONP and CONV."""
     import synth
     out = {}
@@ -379,6 +392,7 @@ def build_table(names=TABLE_MECHS):
             e[f"source_{tag}"] = per_state(m, mode, False, n_states=n_states)
             e[f"jacobian_{tag}"] = per_state(m, mode, True, n_states=n_states)
         e["lu"] = lu_counts(m) if m.n_species < 200 else None
+        e["newton_lu"] = newton_lu_counts(m) if m.n_species < 200 else None
         out[name] = e
     return out
 

@@ -39,6 +39,7 @@ struct pj_plan {
   };
   std::vector<Group> groups;
   int tpb = 128, bps = 1, use_smem = 1;
+  pj::CoopPlan coop{};  // tpb 256 / 512: the cooperative Jacobian kernel
   int grid = 0;
   size_t smem = 0;
   double* ws = nullptr;
@@ -49,13 +50,7 @@ struct pj_plan {
 
 namespace pj {
 
-struct BatchDev {
-  const double* param;
-  const double* phi;
-  double* out;
-  double* dphi;
-  int64_t n, ld;
-};
+using BatchDev = CoopBatch;  // (param, phi, out, dphi, n, ld) of one batch
 
 // Persistent kernel: OP 0 = source terms, 1 = analytical Jacobian (FP64).
 template <int OP, int MODE, int FMT, bool SPECIAL>
@@ -103,6 +98,15 @@ __global__ void __launch_bounds__(128, 4) k_batched(DevMech m, const BatchDev* _
 
 template <int OP, int MODE, int FMT>
 static int launch_group(const pj_plan* p, const pj_plan::Group& g, cudaStream_t st) {
+  if (p->coop.use) {
+    // the cooperative kernel (a 32-state tile per block) over the group's
+    // tiles, handed out by the same counter
+    cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(plan counter)");
+    JacArgs a{nullptr, nullptr, 0, nullptr, nullptr, p->d_status, nullptr, 0.0,
+              CoopSrc{static_cast<const CoopBatch*>(g.d_batches), g.d_tile_start, (int)g.idx.size(), g.d_counter}};
+    return launch_jac_coop_f64(p->mech->dm, p->coop, MODE, FMT, g.tiles * 32, a, p->ws, st);
+  }
   auto kern = p->mech->dm.nr_plain < p->mech->dm.nr ? k_batched<OP, MODE, FMT, true> : k_batched<OP, MODE, FMT, false>;
   cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return check_cuda(e, "cudaMemsetAsync(plan counter)");
@@ -167,8 +171,45 @@ static void drop_graph(pj_plan* p) {
 
 // Apply a launch shape: grid, shared memory or workspace (reallocated when it
 // must grow).
+static int64_t plan_max_tiles(const pj_plan* p) {
+  int64_t t = 0;
+  for (const auto& g : p->groups) t = std::max(t, g.tiles);
+  return t;
+}
+
+// workspace of at least `need` bytes (reallocated when it must grow)
+static int plan_workspace(pj_plan* p, size_t need) {
+  if (need <= p->ws_bytes) return PJ_OK;
+  if (p->ws) cudaFree(p->ws);
+  p->ws = nullptr;
+  p->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&p->ws, need);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(plan workspace)");
+  p->ws_bytes = need;
+  return PJ_OK;
+}
+
 static int plan_configure(pj_plan* p, int tpb, int bps, int use_smem) {
-  if (tpb != 32 && tpb != 64 && tpb != 128) return fail(PJ_ERR_ARG, "plan: threads per block must be 32, 64 or 128");
+  if (tpb == 256 || tpb == 512) {
+    // cooperative: tpb / 32 warps share each 32-state tile
+    if (p->op != 1) return fail(PJ_ERR_UNSUPPORTED, "plan: the cooperative layout computes Jacobians only");
+    CoopPlan c{};
+    if (!coop_shape(p->mech->dm, tpb / 32, bps, use_smem != 0, plan_max_tiles(p), c))
+      return fail(PJ_ERR_UNSUPPORTED, "plan: cooperative shape does not fit (blocks x warps <= 16 per SM, "
+                                      "shared memory)");
+    drop_graph(p);
+    int rc = plan_workspace(p, c.ws_bytes);
+    if (rc) return rc;
+    p->tpb = tpb;
+    p->bps = bps;
+    p->use_smem = use_smem ? 1 : 0;
+    p->coop = c;
+    p->grid = c.grid;
+    p->smem = c.smem;
+    return PJ_OK;
+  }
+  if (tpb != 32 && tpb != 64 && tpb != 128)
+    return fail(PJ_ERR_ARG, "plan: threads per block must be 32, 64 or 128 (256 or 512: cooperative)");
   if (bps < 1 || bps > 16) return fail(PJ_ERR_ARG, "plan: blocks per SM must be 1..16");
   const size_t per_thread = (size_t)plan_arrays(p) * p->mech->ns * sizeof(double);
   const size_t smem_cap = 225 * 1024;
@@ -178,23 +219,11 @@ static int plan_configure(pj_plan* p, int tpb, int bps, int use_smem) {
   p->tpb = tpb;
   p->bps = bps;
   p->use_smem = use_smem;
+  p->coop = CoopPlan{};
   p->grid = sm_count() * bps;
   p->smem = use_smem ? per_thread * tpb : 0;
-  if (use_smem) {
-    int rc = dispatch(p->op, p->mode, p->fmt, SetSmem{p->mech->dm, p->smem});
-    if (rc) return rc;
-  } else {
-    const size_t need = per_thread * (size_t)p->grid * tpb;
-    if (need > p->ws_bytes) {
-      if (p->ws) cudaFree(p->ws);
-      p->ws = nullptr;
-      p->ws_bytes = 0;
-      cudaError_t e = cudaMalloc(&p->ws, need);
-      if (e != cudaSuccess) return check_cuda(e, "cudaMalloc(plan workspace)");
-      p->ws_bytes = need;
-    }
-  }
-  return PJ_OK;
+  if (use_smem) return dispatch(p->op, p->mode, p->fmt, SetSmem{p->mech->dm, p->smem});
+  return plan_workspace(p, per_thread * (size_t)p->grid * tpb);
 }
 
 static void plan_release(pj_plan* p) {
@@ -334,12 +363,18 @@ extern "C" int pj_plan_create(const pj_mech* m, int op, int mode, int fmt, int n
     }
   }
   if (!rc) {
-    // default shape: shared memory when 128 threads' arrays fit, else a global
-    // workspace with 4 resident blocks of 128 per SM
+    // default shape: shared memory when 128 threads' arrays fit; else, for
+    // the Jacobian, the cooperative layout (16 warps a block, arrays in
+    // shared memory where they fit, else in the workspace: one 32-state tile
+    // per SM keeps them in L2), for source terms a global workspace with 4
+    // resident blocks of 128 per SM
     const size_t per_thread = (size_t)plan_arrays(p) * m->ns * sizeof(double);
     const int fit = (int)((225 * 1024 / per_thread) / 32 * 32);
     if (fit >= 128) rc = plan_configure(p, fit >= 256 ? 128 : (fit % 64 == 0 ? 64 : 32), 1, 1);
-    else rc = plan_configure(p, 128, 4, 0);
+    else if (p->op == 1) {
+      rc = plan_configure(p, 512, 1, 1);
+      if (rc == PJ_ERR_UNSUPPORTED) rc = plan_configure(p, 512, 1, 0);
+    } else rc = plan_configure(p, 128, 4, 0);
   }
   if (rc) {
     plan_release(p);
@@ -424,6 +459,11 @@ extern "C" int pj_plan_autotune(pj_plan* p, void* stream, const char* cache_path
         if (!sm && per_thread * (size_t)tpb * bps * sm_count() > (size_t(8) << 30)) continue;  // workspace <= 8 GiB
         cands.push_back({tpb, bps, sm});
       }
+  if (p->op == 1)  // the cooperative shapes (those that do not fit are skipped)
+    for (int sm : {1, 0}) {
+      cands.push_back({512, 1, sm});
+      cands.push_back({256, 2, sm});
+    }
   if (cands.empty()) cands.push_back({128, 1, 0});
   cudaEvent_t a, b;
   cudaEventCreate(&a);

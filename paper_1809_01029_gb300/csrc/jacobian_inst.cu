@@ -25,9 +25,10 @@ constexpr bool kInstNewton = false;
 #if PJ_INST_TM == 3
 using InstPlan = CoopPlan;
 template <int MODE, int FMT>
-static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double*, cudaStream_t st) {
-  if (m.nr_plain < m.nr) return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, true>(m, p, n, a, st);
-  return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, false>(m, p, n, a, st);
+static int inst_launch(const DevMech& m, const InstPlan& p, int64_t n, const JacArgs& a, double* ws,
+                       cudaStream_t st) {
+  if (m.nr_plain < m.nr) return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, true>(m, p, n, a, ws, st);
+  return launch_jac_coop_s<MODE, FMT, InstDT, kInstNewton, false>(m, p, n, a, ws, st);
 }
 #elif PJ_INST_TM < 0
 using InstPlan = LaunchPlan;

@@ -119,20 +119,30 @@ enum CoopPart { pAcc, pDen, pDden, pNum, pSum, pOm, pAT_T, pAT_S, pAS_T, pAS_S, 
 // per-state flags (int): valid T, V, P; valid state
 enum CoopFlag { fOk0, fOk, kCoopFlag };
 
-__host__ __device__ constexpr size_t coop_smem_bytes(int ns, int warps) {
-  return (size_t)(3 * ns + kCoopSc + kCoopPart * warps) * kCoopTile * sizeof(double) +
+// per-state arrays C_k, g_k/RT then Cx_k, h_k/RT of a tile: [3][Ns][32] doubles
+__host__ __device__ constexpr size_t coop_arrays_bytes(int ns) {
+  return (size_t)3 * ns * kCoopTile * sizeof(double);
+}
+
+__host__ __device__ constexpr size_t coop_smem_bytes(int ns, int warps, bool arrays_smem = true) {
+  return (arrays_smem ? coop_arrays_bytes(ns) : 0) +
+         (size_t)(kCoopSc + kCoopPart * warps) * kCoopTile * sizeof(double) +
          (size_t)(kCoopFlag * kCoopTile + 2) * sizeof(int);
 }
 
 // MAXW: the most warps a block of this instance has (launch bound MAXW * 32
 // threads, one block per SM guaranteed): 16 caps registers at 128 per
 // thread, 8 allows 255.
+// aws: the per-state arrays of each block's tile in a global workspace
+// (mechanisms too large for shared memory), else null.  src.batches: tiles
+// of several batches from a counter, else the tiles of (n, param, phi, ...).
 template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL, int MAXW>
 __global__ void __launch_bounds__(MAXW * 32, 1)
-    k_jacobian_coop(DevMech m, int64_t n, const double* __restrict__ param, const double* __restrict__ phi,
-                    int64_t ld, DT* __restrict__ J, double* __restrict__ dphi, int* status,
-                    const double* __restrict__ hstep, double gamma) {
+    k_jacobian_coop(DevMech m, int64_t n0, const double* __restrict__ param0, const double* __restrict__ phi0,
+                    int64_t ld0, DT* __restrict__ J0, double* __restrict__ dphi0, int* status,
+                    const double* __restrict__ hstep, double gamma, double* __restrict__ aws, CoopSrc src) {
   PJ_DYN_SMEM;
+  __shared__ int64_t s_tile;
   load_exp_table(m.exp_tab);
   const int ns = m.ns, N = m.N, bath = m.ns - 1;
   // the warp index broadcast from lane 0, so that the compiler knows it (and
@@ -141,9 +151,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
   const int lane = threadIdx.x & 31, warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
   const int W = blockDim.x >> 5;
   const int64_t n_out = FMT == PJ_DENSE ? (int64_t)N * N : (int64_t)m.nnz;
-  double* __restrict__ sc = smem + 3 * ns * kCoopTile + lane;                      // sc[v*32]
-  double* __restrict__ part = smem + (3 * ns + kCoopSc) * kCoopTile + lane;        // part[(w*kCoopPart + v)*32]
-  int* __restrict__ flags = reinterpret_cast<int*>(smem + (3 * ns + kCoopSc + kCoopPart * W) * kCoopTile);
+  double* const tsm = aws ? smem : smem + 3 * ns * kCoopTile;                     // the tile's scalars and sums
+  double* __restrict__ sc = tsm + lane;                                            // sc[v*32]
+  double* __restrict__ part = tsm + kCoopSc * kCoopTile + lane;                    // part[(w*kCoopPart + v)*32]
+  int* __restrict__ flags = reinterpret_cast<int*>(tsm + (kCoopSc + kCoopPart * W) * kCoopTile);
   int* __restrict__ next_rxn = flags + kCoopFlag * kCoopTile;  // the next reaction to hand out
   auto F = [&](int v) -> int& { return flags[v * kCoopTile + lane]; };
   auto S = [&](int v) -> double& { return sc[v * kCoopTile]; };
@@ -155,11 +166,40 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
   };
   StateArrays A;
   A.ns = ns;
-  A.base = smem + lane;
+  A.base = aws ? aws + (int64_t)blockIdx.x * 3 * ns * kCoopTile + lane : smem + lane;
   A.stride = kCoopTile;
   enum { aC = 0, aG = 1, aH = 2 };
 
-  for (int64_t tile = blockIdx.x; tile * kCoopTile < n; tile += gridDim.x) {
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    int64_t tile = it, n = n0, ld = ld0;
+    const double* __restrict__ param = param0;
+    const double* __restrict__ phi = phi0;
+    DT* __restrict__ J = J0;
+    double* __restrict__ dphi = dphi0;
+    if (src.batches) {
+      // the next tile of the plan (read by every thread before the block's
+      // next barrier, rewritten only after several more)
+      if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(src.counter, 1ULL);
+      __syncthreads();
+      tile = s_tile;
+      if (tile >= __ldg(src.tile_start + src.nb)) break;
+      int lo = 0, hi = src.nb - 1;  // the batch holding it: the last b with tile_start[b] <= tile
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(src.tile_start + mid) <= tile) lo = mid;
+        else hi = mid - 1;
+      }
+      const CoopBatch B = src.batches[lo];
+      tile -= __ldg(src.tile_start + lo);
+      n = B.n;
+      ld = B.ld;
+      param = B.param;
+      phi = B.phi;
+      J = reinterpret_cast<DT*>(B.out);
+      dphi = B.dphi;
+    } else if (tile * kCoopTile >= n) {
+      break;
+    }
     const int64_t s = tile * kCoopTile + lane;
     const bool act = s < n;
     double* __restrict__ wrow = dphi + 2 * ld + s;
@@ -415,15 +455,18 @@ static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const 
 }
 
 template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL>
-static int launch_jac_coop_s(const DevMech& m, const CoopPlan& c, int64_t n, const JacArgs& a, cudaStream_t st) {
+static int launch_jac_coop_s(const DevMech& m, const CoopPlan& c, int64_t n, const JacArgs& a, double* ws,
+                             cudaStream_t st) {
   auto kern = c.wide_regs ? k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, 8>
                           : k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, kCoopWarpsMax>;
   int rc;
   if ((rc = set_smem(kern, c.smem))) return rc;
+  // n: the states of the launch's batch, or (batched) 32 x the plan's tiles
   const int64_t tiles = (n + kCoopTile - 1) / kCoopTile;
   const int64_t grid = tiles < c.grid ? (tiles < 1 ? 1 : tiles) : c.grid;
   kern<<<(unsigned)grid, c.warps * 32, c.smem, st>>>(m, n, a.param, a.phi, a.ld, static_cast<DT*>(a.J), a.dphi,
-                                                     a.status, a.hstep, a.gamma);
+                                                     a.status, a.hstep, a.gamma, c.ws_bytes ? ws : nullptr,
+                                                     a.src);
   return check_cuda(cudaGetLastError(), "k_jacobian_coop launch");
 }
 #endif  // PJ_NO_LAUNCHERS

@@ -17,8 +17,10 @@
 //    on the same reaction), so there is no divergence except the NASA range.
 //  * Jacobian entries are accumulated with fire-and-forget FP64 reductions
 //    into the zero-initialised output at L2 (no read-modify-write latency on
-//    the SM and no FP64 add on the SM); each entry is owned by one thread,
-//    whose reductions apply in program order, so results are deterministic.
+//    the SM and no FP64 add on the SM).  One state per thread, each entry is
+//    owned by one thread, whose reductions apply in program order, so results
+//    are deterministic; the cooperative layout sums one entry from several
+//    warps, in an order that can change between runs.
 //    Targets come from a static full -> sparse index map built at mechanism
 //    load (the mapping Sec. 3.4 proposes instead of a per-entry search).
 //  * This file holds the source-term kernel and the launch planning; the
@@ -212,49 +214,74 @@ TmPlan tm_plan(int ns) {
 // block, one block per SM at 16 warps: 44 KB of DRAM traffic per state at 53
 // species against 154 KB), so it is the layout to force where the Jacobian
 // shares the GPU with other memory-heavy work.
+// The cooperative kernel keeps a tile's per-state arrays in shared memory
+// where they fit, else (more than about 200 species) in a workspace of 3 Ns
+// x 32 doubles per block, which at one block per SM stays in L2.
 // PYJAC_GB_JAC_LAYOUT=coop|percore forces one family (coop only where its
 // shared memory fits); PYJAC_GB_COOP_WARPS sets the warps per block (4, 8
-// or 16) and PYJAC_GB_COOP_CTAS the blocks per SM (at most 16 / warps); 8
-// warps in one block per SM run the instance compiled for 255 registers.
+// or 16), PYJAC_GB_COOP_CTAS the blocks per SM (at most 16 / warps) and
+// PYJAC_GB_COOP_ARRAYS=global puts the arrays in the workspace; 8 warps in
+// one block per SM run the instance compiled for 255 registers.
 static int env_int(const char* name, int dflt) {
   const char* v = getenv(name);
   return v && *v ? atoi(v) : dflt;
 }
 
-static bool coop_shape(const DevMech& m, int warps, int ctas, CoopPlan& c) {
-  c = CoopPlan{false, warps, ctas, coop_smem_bytes(m.ns, warps), sm_count() * ctas, warps == 8 && ctas == 1};
+bool coop_shape(const DevMech& m, int warps, int ctas, bool arrays_smem, int64_t tiles, CoopPlan& c) {
+  c = CoopPlan{false, warps, ctas, coop_smem_bytes(m.ns, warps, arrays_smem), sm_count() * ctas,
+               warps == 8 && ctas == 1, 0};
   if (warps != 4 && warps != 8 && warps != 16) return false;
   if (ctas < 1 || ctas * warps > 16) return false;
   if (c.smem + kBlockOverhead > kSmemPerSm / (size_t)ctas || c.smem > kSmemCap) return false;
+  if (!arrays_smem) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, c.grid));
+    c.ws_bytes = coop_arrays_bytes(m.ns) * (size_t)blocks;
+  }
   c.use = true;
   return true;
 }
 
+// per-state arrays in shared memory where they fit, else in the workspace
+static bool coop_fit(const DevMech& m, int warps, int ctas, int64_t n, CoopPlan& c) {
+  const int64_t tiles = (n + kCoopTile - 1) / kCoopTile;
+  return coop_shape(m, warps, ctas, true, tiles, c) || coop_shape(m, warps, ctas, false, tiles, c);
+}
+
 CoopPlan coop_plan(const DevMech& m, int fmt, int dt_bytes, int64_t n) {
   (void)fmt;
-  CoopPlan c{false, 16, 1, 0, 0, false};
+  CoopPlan c{false, 16, 1, 0, 0, false, 0};
   const char* lay = getenv("PYJAC_GB_JAC_LAYOUT");
   if (lay && strcmp(lay, "percore") == 0) return c;
   if (lay && strcmp(lay, "coop") == 0) {
-    const int warps = env_int("PYJAC_GB_COOP_WARPS", 16);
-    coop_shape(m, warps, env_int("PYJAC_GB_COOP_CTAS", 16 / std::max(warps, 1)), c);
+    const int warps = env_int("PYJAC_GB_COOP_WARPS", 16), ctas = env_int("PYJAC_GB_COOP_CTAS", 16 / std::max(warps, 1));
+    const char* ar = getenv("PYJAC_GB_COOP_ARRAYS");
+    if (ar && strcmp(ar, "global") == 0) coop_shape(m, warps, ctas, false, (n + kCoopTile - 1) / kCoopTile, c);
+    else coop_fit(m, warps, ctas, n, c);
     return c;
   }
   const TmPlan t = tm_plan(m.ns);
   const bool percore_global = !t.use && plan_for(jacobian_arrays(), m.ns, n).global_ws;
   if (n < (int64_t)sm_count() * 512 || percore_global) {
-    coop_shape(m, 16, 1, c);
+    coop_fit(m, 16, 1, n, c);
     return c;
   }
-  if (t.use && dt_bytes == 4 && coop_shape(m, 8, 2, c)) return c;
+  if (t.use && dt_bytes == 4 && coop_shape(m, 8, 2, true, 0, c)) return c;
   c.use = false;
   return c;
 }
 
 size_t workspace_bytes(int arrays, int ns, int64_t n) {
   if (arrays == jacobian_arrays()) {
+    // the most any layout can need: the one-state-per-thread plans, or the
+    // cooperative one with its arrays in the workspace
     const TmPlan t = tm_plan(ns);
-    if (t.use) return t.ws_bytes;
+    const size_t pc = t.use ? t.ws_bytes : plan_for(arrays, ns, n).ws_bytes;
+    // (any shape that may not fit its arrays in shared memory: at most 4
+    // blocks per SM, since a block has 4 warps or more)
+    const int64_t tiles =
+        std::max<int64_t>(1, std::min<int64_t>((n + kCoopTile - 1) / kCoopTile, (int64_t)sm_count() * 4));
+    const size_t co = coop_smem_bytes(ns, kCoopWarpsMax) <= kSmemCap ? 0 : coop_arrays_bytes(ns) * (size_t)tiles;
+    return std::max(pc, co);
   }
   return plan_for(arrays, ns, n).ws_bytes;
 }
@@ -264,7 +291,12 @@ size_t workspace_bytes(int arrays, int ns, int64_t n) {
 static int launch_jac_any(const DevMech& m, int mode, int fmt, int64_t n, const JacArgs& a, bool f32, void* work,
                           size_t work_bytes, cudaStream_t st) {
   const CoopPlan c = coop_plan(m, fmt, f32 ? 4 : 8, n);
-  if (c.use) return (f32 ? launch_jac_coop_f32 : launch_jac_coop_f64)(m, c, mode, fmt, n, a, nullptr, st);
+  if (c.use) {
+    if (c.ws_bytes && (!work || work_bytes < c.ws_bytes))
+      return fail(PJ_ERR_NOMEM, "workspace too small for the Jacobian kernel (see pj_workspace_size)");
+    return (f32 ? launch_jac_coop_f32 : launch_jac_coop_f64)(m, c, mode, fmt, n, a, static_cast<double*>(work),
+                                                            st);
+  }
   const TmPlan t = tm_plan(m.ns);
   if (t.use) {
     if (t.ws_bytes && (!work || work_bytes < t.ws_bytes))

@@ -47,7 +47,30 @@ struct CoopPlan {
   size_t smem;
   int grid;
   bool wide_regs;   // 8 warps, one block per SM, up to 255 registers a thread
+  size_t ws_bytes;  // per-state arrays in a global workspace (grid x 3 Ns x 32
+                    // doubles); 0: in shared memory
 };
+
+// Tiles of several batches handed out by a block counter (the batched
+// plans), instead of consecutive tiles of the one batch a launch is given.
+struct CoopBatch {
+  const double* param;
+  const double* phi;
+  double* out;
+  double* dphi;
+  int64_t n, ld;
+};
+struct CoopSrc {
+  const CoopBatch* batches;     // null: the launch's own batch
+  const int64_t* tile_start;    // [nb + 1] first tile of each batch
+  int nb;
+  unsigned long long* counter;  // zeroed before the launch
+};
+
+// Shape the cooperative layout: `warps` (4, 8, 16) warps per block, `ctas`
+// blocks per SM, per-state arrays in shared memory (arrays_smem) or in a
+// global workspace; false when it does not fit.  tiles bounds the grid.
+bool coop_shape(const DevMech& m, int warps, int ctas, bool arrays_smem, int64_t tiles, CoopPlan& c);
 
 constexpr size_t kSmemPerSm = 228 * 1024;                    // shared memory per SM
 constexpr size_t kSmemCap = 225 * 1024;                      // per block, less the 2 KB exp table
@@ -108,6 +131,7 @@ struct JacArgs {
   int* status;
   const double* hstep;
   double gamma;
+  CoopSrc src;  // cooperative layout only; zero: tiles of this batch
 };
 
 // Jacobian launchers, one translation unit each (jacobian_inst.cu built once

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "kinetics_device.cuh"
 #include "launch.h"
@@ -274,17 +276,16 @@ __global__ void __launch_bounds__(256) k_lu_factor_v(DevLu L, int64_t n, const T
   __shared__ V s_inv;
   __shared__ T s_hg[S];
   auto at = [&](int p, int q) -> T& { return reinterpret_cast<T*>(A + p)[q]; };
-  // warp 0: 1 / pivot c (all S states), stored in the diagonal slot and
-  // broadcast; then column c's entries below the pivot scaled by it
+  // warp 0: 1 / pivot c, lane q for state q (one warp instruction stream for
+  // all S states), stored in the diagonal slot and broadcast; then column
+  // c's entries below the pivot scaled by it
   auto finish_column = [&](int c) {
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < S; q++) {
-        const T piv = at(c * NP + c, q);
-        if (bad_pivot(piv)) bad[q] = 1;
-        reinterpret_cast<T*>(&s_inv)[q] = T(1) / piv;
-      }
-      A[c * NP + c] = s_inv;
+    if (lane < S) {
+      const T piv = at(c * NP + c, lane);
+      if (bad_pivot(piv)) bad[lane] = 1;
+      const T r = T(1) / piv;
+      reinterpret_cast<T*>(&s_inv)[lane] = r;
+      at(c * NP + c, lane) = r;
     }
     __syncwarp();
     const V inv = s_inv;

@@ -49,12 +49,19 @@ def pytest_terminal_summary(terminalreporter):
     error above rtol |ref| but within rtol env), and the well-conditioned
     entries (env <= 10 |ref|) that met the plain per-entry bar."""
     try:
-        from tests.parity import REPORT
+        from tests.parity import REPORT, NEWTON_REPORT
     except Exception:
         return
+    tr = terminalreporter
+    if NEWTON_REPORT:
+        tr.write_sep("-", "FP32 Newton matrix against the FP64 oracle")
+        for r in NEWTON_REPORT:
+            tr.write_line(f"  {r['what']}: {r['entries']} entries of {r['states']} states; |dM| / (|M| + h gamma "
+                          f"env): median {r['entry_median']:.2e}, p99 {r['entry_p99']:.2e}, max "
+                          f"{r['entry_max']:.2e}; ||dM||_F / ||M||_F median {r['frob_median']:.2e}, max "
+                          f"{r['frob_max']:.2e}")
     if not REPORT:
         return
-    tr = terminalreporter
     ent = sum(r["entries"] for r in REPORT)
     env = sum(r["needed_env"] for r in REPORT)
     well = sum(r["well"] for r in REPORT)

@@ -33,6 +33,27 @@ def newton_tol(scale):
     return NEWTON_ENTRY * np.asarray(scale) + NEWTON_FLOOR
 
 
+# the FP32 Newton form's measured error against the FP64 oracle, one record
+# per check (printed at the end of the test session)
+NEWTON_REPORT = []
+
+
+def newton_error(got, ref, scale, what=""):
+    """Record the error of FP32 Newton-matrix values `got` against the
+    oracle's M = I - h gamma J (`ref`, entries x states) in the terms of the
+    stated accuracy: per entry |dM| / (|M| + h gamma env(J)) (`scale`), and
+    per state the Frobenius error ||dM||_F / ||M||_F."""
+    got, ref, scale = (np.asarray(a, dtype=np.float64) for a in (got, ref, scale))
+    err = np.abs(got - ref)
+    rel = err / np.maximum(scale, NEWTON_FLOOR)
+    frob = np.sqrt((err ** 2).sum(axis=0)) / np.sqrt((ref ** 2).sum(axis=0))
+    rec = dict(what=what, entries=int(err.size), states=int(err.shape[-1]),
+               entry_median=float(np.median(rel)), entry_p99=float(np.quantile(rel, 0.99)),
+               entry_max=float(rel.max()), frob_median=float(np.median(frob)), frob_max=float(frob.max()))
+    NEWTON_REPORT.append(rec)
+    return rec
+
+
 # one record per check_close call: what, entries, entries that passed only
 # through the envelope, well-conditioned entries, largest relative error of a
 # well-conditioned entry
@@ -172,15 +193,23 @@ def y_envelope(m, mode, phi, par):
 def jacobian_layout(name):
     """Run the library's Jacobian entries with one kernel family: "coop" (the
     warps of a block share 32 states; L2-resident accumulation, rounding
-    depends on the order of cross-warp reductions) or "percore" (one state
-    per thread; bit-reproducible).  The library reads PYJAC_GB_JAC_LAYOUT at
-    every launch."""
-    old = os.environ.get("PYJAC_GB_JAC_LAYOUT")
-    os.environ["PYJAC_GB_JAC_LAYOUT"] = name
+    depends on the order of cross-warp reductions), "coop-global" (the same
+    with the tile's per-state arrays in the workspace instead of shared
+    memory) or "percore" (one state per thread; bit-reproducible).  The
+    library reads PYJAC_GB_JAC_LAYOUT and PYJAC_GB_COOP_ARRAYS at every
+    launch."""
+    keys = ("PYJAC_GB_JAC_LAYOUT", "PYJAC_GB_COOP_ARRAYS")
+    old = {k: os.environ.get(k) for k in keys}
+    os.environ["PYJAC_GB_JAC_LAYOUT"] = "coop" if name.startswith("coop") else name
+    if name == "coop-global":
+        os.environ["PYJAC_GB_COOP_ARRAYS"] = "global"
+    else:
+        os.environ.pop("PYJAC_GB_COOP_ARRAYS", None)
     try:
         yield
     finally:
-        if old is None:
-            os.environ.pop("PYJAC_GB_JAC_LAYOUT", None)
-        else:
-            os.environ["PYJAC_GB_JAC_LAYOUT"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 import synth
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope, paper_error_norms, newton_tol
+from tests.parity import (RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope, paper_error_norms,
+                          newton_tol, newton_error)
 
 pytestmark = pytest.mark.gpu
 
@@ -164,6 +165,7 @@ def test_usc111_quarter_mebi_states_newton_and_jacobian(pj, mechs):
     conv = lambda a: oracle.dense_to_csr_values(m, a)
     err = np.abs(got - conv(M_ref[..., keep]))
     tol = newton_tol(conv(scale[..., keep]))
+    newton_error(got, conv(M_ref[..., keep]), conv(scale[..., keep]), "usc111, 256 ki states (sampled)")
     assert np.all(err <= tol), float(np.max(err / tol))
     del M
     Jd = torch.empty((h.nnz, n), dtype=torch.float64, device="cuda")

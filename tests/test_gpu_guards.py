@@ -69,7 +69,7 @@ NOMEM_CASES = [
     ("jacobian", "gri53", "percore"),
     ("jacobian", "usc111", "percore"),   # the cooperative layout needs no workspace
     ("newton", "usc111", "percore"),
-    ("eval_y", "usc111", None),     # 53 species: y's arrays fit shared memory, no workspace
+    ("eval_y", "ic5874", None),     # up to 112 species y's arrays fit shared memory
     ("vjp", "gri53", None),
     ("fd", "gri53", None),
     ("lu", "ic5874", None),
@@ -126,7 +126,26 @@ def test_workspace_one_byte_short_is_rejected(pj, mechs, what, name, layout):
         assert all(g.intact() and bool((g.t == g.canary).all()) for g in outs), "outputs touched after a rejection"
 
 
-@pytest.mark.parametrize("layout", ["coop", "percore"])
+@pytest.mark.parametrize("name,layout", [("usc111", "coop-global"), ("ic5874", "coop")])
+def test_cooperative_workspace_arrays_need_the_workspace(pj, mechs, name, layout):
+    """The cooperative layout with its per-state arrays in the workspace (874
+    species by default, any mechanism when forced) rejects a call without a
+    workspace, launches nothing and leaves the outputs untouched."""
+    m = mechs(name)
+    h = pj.pj_mech_create(m)
+    n = 40
+    assert h.workspace_size(pj.PJ_OP_JACOBIAN, n) > 0
+    phi, par, _, _ = _states(m, n, n, synth.CONP, 75)
+    v, d = Guarded(h.nnz, n, n), Guarded(m.n_species + 1, n, n)
+    with jacobian_layout(layout), pytest.raises(pj.PJError) as e:
+        pj.pj_eval_jacobian_sparse(h, synth.CONP, pj.PJ_CSR, n, par, phi, n, v.t, d.t, None, None, 0)
+    assert e.value.code == N.PJ_ERR_NOMEM
+    import torch
+    torch.cuda.synchronize()
+    assert v.intact() and d.intact() and bool((v.t == v.canary).all())
+
+
+@pytest.mark.parametrize("layout", ["coop", "coop-global", "percore"])
 @pytest.mark.parametrize("name", ["gri53_types", "usc111"])
 def test_guard_bands_jacobian_entries(pj, mechs, name, layout):
     """Source terms, CSR / CSC / dense Jacobian and the FP32 Newton matrix of

@@ -15,11 +15,12 @@ import pytest
 import oracle
 import synth
 from tests import tiny_mechs as tm
-from tests.parity import RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, jacobian_layout, newton_tol
+from tests.parity import (RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, jacobian_layout, newton_tol,
+                          newton_error)
 
 pytestmark = pytest.mark.gpu
 
-LAYOUTS = ["coop", "percore"]
+LAYOUTS = ["coop", "coop-global", "percore"]
 
 
 @pytest.fixture(scope="module")
@@ -147,8 +148,10 @@ def test_layout_newton_matrix_f32(pj, mechs, name, n, layout):
     with jacobian_layout(layout):
         M = pj.newton_matrix_f32(h, synth.CONP, to_dev(phi), to_dev(par), to_dev(hs), 1.0,
                                  fmt=pj.PJ_CSR).cpu().numpy().astype(np.float64)
-    err = np.abs(M - oracle.dense_to_csr_values(m, M_ref))
+    ref = oracle.dense_to_csr_values(m, M_ref)
+    err = np.abs(M - ref)
     tol = newton_tol(oracle.dense_to_csr_values(m, scale))
+    newton_error(M, ref, oracle.dense_to_csr_values(m, scale), f"{name}, {n} states, {layout}")
     assert np.all(err <= tol), float(np.max(err / tol))
 
 

@@ -655,6 +655,12 @@ def build_ragged(pj, synth, torch, dev, stream, scale=1.0, config=None, group_st
             "total": sum(sizes), "keep": (batches, pool, fpool)}
 
 
+def plan_kernel(plan):
+    """The kernel a batched plan's launch shape runs: 256 or 512 threads per
+    block are the cooperative layout."""
+    return "k_jacobian_coop" if plan.config()["threads_per_block"] >= 256 else "k_batched"
+
+
 def ragged_workload(pj, synth, torch, dev, stream):
     """States/s of the 874-species ragged workload (see build_ragged), timed
     by graph replay."""
@@ -738,10 +744,10 @@ def run_ragged(args, rank, world, local, torch, dist, synth, pj):
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_DFMA_PER_CLK_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G DFMA-equiv/s (FP64 pipe)",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_batched", "work_per_state": fp64_work,
+                "frac": achieved / peak, "traffic": None, "kernel": plan_kernel(plan), "work_per_state": fp64_work,
                 "work_source": "oracle operation count (oracle/work_counts.json)", "counts": counts,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock"}
-    tr = kernel_traffic("ragged", "ic5874", "k_batched")
+    tr = kernel_traffic("ragged", "ic5874", plan_kernel(plan))
     if tr is not None:
         roofline["traffic"] = tr * n
         roofline["traffic_source"] = "ncu dram bytes per state of the current kernel sources x states"

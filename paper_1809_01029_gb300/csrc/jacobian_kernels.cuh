@@ -136,7 +136,7 @@ __host__ __device__ constexpr size_t coop_smem_bytes(int ns, int warps, bool arr
 // aws: the per-state arrays of each block's tile in a global workspace
 // (mechanisms too large for shared memory), else null.  src.batches: tiles
 // of several batches from a counter, else the tiles of (n, param, phi, ...).
-template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL, int MAXW>
+template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL, int MAXW, bool BATCHED = false>
 __global__ void __launch_bounds__(MAXW * 32, 1)
     k_jacobian_coop(DevMech m, int64_t n0, const double* __restrict__ param0, const double* __restrict__ phi0,
                     int64_t ld0, DT* __restrict__ J0, double* __restrict__ dphi0, int* status,
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
     const double* __restrict__ phi = phi0;
     DT* __restrict__ J = J0;
     double* __restrict__ dphi = dphi0;
-    if (src.batches) {
+    if constexpr (BATCHED) {
       // the next tile of the plan (read by every thread before the block's
       // next barrier, rewritten only after several more)
       if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(src.counter, 1ULL);
@@ -457,8 +457,13 @@ static int launch_jac_t(const DevMech& m, const LaunchPlan& p, int64_t n, const 
 template <int MODE, int FMT, typename DT, bool NEWTON, bool SPECIAL>
 static int launch_jac_coop_s(const DevMech& m, const CoopPlan& c, int64_t n, const JacArgs& a, double* ws,
                              cudaStream_t st) {
-  auto kern = c.wide_regs ? k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, 8>
-                          : k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, kCoopWarpsMax>;
+  // the batched plans' tile hand-out is an instance of its own (FP64
+  // Jacobian, up to 16 warps), so that the other instances carry none of its
+  // registers
+  auto kern = a.src.batches ? k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, kCoopWarpsMax, !NEWTON>
+              : c.wide_regs ? k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, 8>
+                            : k_jacobian_coop<MODE, FMT, DT, NEWTON, SPECIAL, kCoopWarpsMax>;
+  if (NEWTON && a.src.batches) return fail(PJ_ERR_UNSUPPORTED, "batched plans compute the FP64 Jacobian only");
   int rc;
   if ((rc = set_smem(kern, c.smem))) return rc;
   // n: the states of the launch's batch, or (batched) 32 x the plan's tiles

@@ -280,7 +280,9 @@ size_t workspace_bytes(int arrays, int ns, int64_t n) {
     // blocks per SM, since a block has 4 warps or more)
     const int64_t tiles =
         std::max<int64_t>(1, std::min<int64_t>((n + kCoopTile - 1) / kCoopTile, (int64_t)sm_count() * 4));
-    const size_t co = coop_smem_bytes(ns, kCoopWarpsMax) <= kSmemCap ? 0 : coop_arrays_bytes(ns) * (size_t)tiles;
+    const char* ar = getenv("PYJAC_GB_COOP_ARRAYS");
+    const bool global = coop_smem_bytes(ns, kCoopWarpsMax) > kSmemCap || (ar && strcmp(ar, "global") == 0);
+    const size_t co = global ? coop_arrays_bytes(ns) * (size_t)tiles : 0;
     return std::max(pc, co);
   }
   return plan_for(arrays, ns, n).ws_bytes;

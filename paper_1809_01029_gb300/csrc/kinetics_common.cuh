@@ -353,23 +353,31 @@ __device__ __forceinline__ double third_body(const DevMech& m, const SA& A, int 
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }  // result unused: red.global.add.f64
 
-// wdot_k += nu_k q for the reaction's species: L2 reductions into wrow[k*ld]
-// for k < Ns-1, the bath gas into a register.
+// wdot_k += nu_k q for the reaction's species.  k < Ns-1: nu_k L2
+// reductions of +-q into wrow[k*ld] (a repeated reduction instead of a
+// multiply: no FP64 instruction, which the compiler would otherwise issue,
+// predicated off, for the common nu = 1 too); skipped when !w.  The bath gas,
+// in few reactions (Rxn::bath_in), into a register under a branch of its own.
 __device__ __forceinline__ void scatter_wdot(const Rxn* __restrict__ r, int nre, int npr, int bath, double q,
-                                             double* wrow, int64_t ld, double& w_bath) {
+                                             double* wrow, int64_t ld, double& w_bath, bool w = true) {
+  const double nq = dneg(q);
 #pragma unroll
   for (int a = 0; a < PJ_MAX_SP; a++) {
     if (a < nre) {
       const int k = __ldg(&r->sp[a]);
-      const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
-      if (k == bath) w_bath -= v;
-      else red_add(wrow + (int64_t)k * ld, dneg(v));
+      if (k != bath && w)
+        for (int u = __ldg(&r->nu[a]); u > 0; u--) red_add(wrow + (int64_t)k * ld, nq);
     }
     if (a < npr) {
       const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
-      const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
-      if (k == bath) w_bath += v;
-      else red_add(wrow + (int64_t)k * ld, v);
+      if (k != bath && w)
+        for (int u = __ldg(&r->nu[PJ_MAX_SP + a]); u > 0; u--) red_add(wrow + (int64_t)k * ld, q);
+    }
+  }
+  if (__ldg(&r->bath_in)) {
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre && __ldg(&r->sp[a]) == bath) w_bath = fma(-__ldg(&r->nud[a]), q, w_bath);
+      if (a < npr && __ldg(&r->sp[PJ_MAX_SP + a]) == bath) w_bath = fma(__ldg(&r->nud[PJ_MAX_SP + a]), q, w_bath);
     }
   }
 }

@@ -66,21 +66,7 @@ __device__ __forceinline__ void source_state(const DevMech& m, const SA& A, cons
       }
     }
     const double q = c * (Rf - Rr);
-#pragma unroll
-    for (int a = 0; a < PJ_MAX_SP; a++) {
-      if (a < nre) {
-        const int k = __ldg(&r->sp[a]);
-        const double v = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
-        if (k == bath) w_bath -= v;
-        else red_add(wrow + (int64_t)k * ld, dneg(v));
-      }
-      if (a < npr) {
-        const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
-        const double v = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
-        if (k == bath) w_bath += v;
-        else red_add(wrow + (int64_t)k * ld, v);
-      }
-    }
+    scatter_wdot(r, nre, npr, bath, q, wrow, ld, w_bath);
   };
   for (int i = 0; i < m.nr_plain; i++) reaction(i, BoolTag<false>{});
   if (SPECIAL)
@@ -130,11 +116,11 @@ __device__ __forceinline__ void jred(DT* J, int64_t e, int64_t ld, int64_t s, DT
 
 __device__ __forceinline__ float dneg(float x) { return -x; }
 
+// +-x for a row's unit coefficient (rows hold |nu| = 1, see RowNu): a sign
+// flip, no FP64 instruction
 template <typename DT>
-__device__ __forceinline__ DT nu_times_t(int nu, double nud, DT x) {
-  if (nu == 1) return x;
-  if (nu == -1) return dneg(x);
-  return DT(nud) * x;
+__device__ __forceinline__ DT nu_times_t(int nu, double, DT x) {
+  return nu > 0 ? x : dneg(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,26 +276,35 @@ __device__ __forceinline__ void jac_reaction(const DevMech& m, const SA& A, JacV
 
   // derivatives of the net rate in T and S (rate constants, and the bath
   // gas through C_Ns = C_tot - sum C_k)
+  // (the bath gas's terms only in reactions that have it, under a branch of
+  // their own: FP64 work under a per-species condition is otherwise issued,
+  // predicated off, for every species)
   DT dRdT = DT(Rf) * dlnkf - DT(Rr) * dlnkr;
   DT dRdS = DT(0);
+  if (MODE == PJ_CONP) {
 #pragma unroll
-  for (int a = 0; a < PJ_MAX_SP; a++) {
-    if (a < nre) {
-      const int k = __ldg(&r->sp[a]);
-      if (k == bath) {
-        dRdT = dRdT + dRf_t[a] * dCb_T_t;
-        dRdS = dRdS + dRf_t[a] * dCb_S_t;
-      } else if (MODE == PJ_CONP) {
-        dRdS = dRdS - dRf_t[a] * (DT(A.at(aC, k)) * invV_t);
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre) {
+        const int k = __ldg(&r->sp[a]);
+        const double ck = k == bath ? 0.0 : A.at(aC, k);  // a select, not a branch
+        dRdS = dRdS - dRf_t[a] * (DT(ck) * invV_t);
+      }
+      if (rev && a < npr) {
+        const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
+        const double ck = k == bath ? 0.0 : A.at(aC, k);
+        dRdS = dRdS + dRr_t[a] * (DT(ck) * invV_t);
       }
     }
-    if (rev && a < npr) {
-      const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
-      if (k == bath) {
+  }
+  if (__ldg(&r->bath_in)) {
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre && __ldg(&r->sp[a]) == bath) {
+        dRdT = dRdT + dRf_t[a] * dCb_T_t;
+        dRdS = dRdS + dRf_t[a] * dCb_S_t;
+      }
+      if (rev && a < npr && __ldg(&r->sp[PJ_MAX_SP + a]) == bath) {
         dRdT = dRdT - dRr_t[a] * dCb_T_t;
         dRdS = dRdS - dRr_t[a] * dCb_S_t;
-      } else if (MODE == PJ_CONP) {
-        dRdS = dRdS + dRr_t[a] * (DT(A.at(aC, k)) * invV_t);
       }
     }
   }
@@ -322,22 +317,7 @@ __device__ __forceinline__ void jac_reaction(const DevMech& m, const SA& A, JacV
   const double q = c * Rn;
   const DT dqdT = c_t * dRdT + Rn_t * dcdT;
   const DT dqdS = c_t * dRdS + Rn_t * dcdS;
-  double* __restrict__ wrow = o.wrow;
-#pragma unroll
-  for (int a = 0; a < PJ_MAX_SP; a++) {
-    if (a < nre) {
-      const int k = __ldg(&r->sp[a]);
-      const double val = nu_times(__ldg(&r->nu[a]), __ldg(&r->nud[a]), q);
-      if (k == bath) v.w_bath -= val;
-      else if (w) red_add(wrow + (int64_t)k * ld, dneg(val));
-    }
-    if (a < npr) {
-      const int k = __ldg(&r->sp[PJ_MAX_SP + a]);
-      const double val = nu_times(__ldg(&r->nu[PJ_MAX_SP + a]), __ldg(&r->nud[PJ_MAX_SP + a]), q);
-      if (k == bath) v.w_bath += val;
-      else if (w) red_add(wrow + (int64_t)k * ld, val);
-    }
-  }
+  scatter_wdot(r, nre, npr, bath, q, o.wrow, ld, v.w_bath, w);
 
   // energy-row and state-row weights of this reaction
   const DT dE = DT(RU * T * (MODE == PJ_CONP ? dh : dh - __ldg(&r->dnu)));
@@ -374,13 +354,10 @@ __device__ __forceinline__ void jac_reaction(const DevMech& m, const SA& A, JacV
     if (w) jred(J, e1, ld, s, nu_times_t<DT>(rn.nu, rn.nud, VdqdS));
   }
 
-  // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i
-  DT Bi = DT(0);
+  // species columns: V dq/dn_j = c dR/dC_j + R dc/dM (alpha_j - 1) + B_i;
+  // the bath gas's own terms make B_i (below, dense reactions only)
   auto slot = [&](int j, DT val) {
-    if (j == bath) {
-      Bi = Bi - val;
-      return;
-    }
+    if (j == bath) return;
     const DT vs = nscale<NEWTON>(o, val);
     for (int q2 = row_lo; q2 < row_hi; q2++) {
       const RowNu rn = m.rows[q2];
@@ -404,6 +381,19 @@ __device__ __forceinline__ void jac_reaction(const DevMech& m, const SA& A, JacV
     }
   }
   if (__ldg(&r->dense)) {
+    // B_i: minus the terms the slots above have for the bath gas, in their order
+    DT Bi = DT(0);
+    for (int a = 0; a < PJ_MAX_SP; a++) {
+      if (a < nre && __ldg(&r->sp[a]) == bath) Bi = Bi - c_t * dRf_t[a];
+      if (rev && a < npr && __ldg(&r->sp[PJ_MAX_SP + a]) == bath) Bi = Bi - dneg(c_t * dRr_t[a]);
+    }
+    if (has_third_body(kind)) {
+      const DT t = Rn_t * dcdM;
+      for (int e = __ldg(&r->eff_lo), eh = __ldg(&r->eff_hi); e < eh; e++) {
+        if (!PJ_DBG_OK(m.dbg, e >= 0 && e < m.n_eff, PJ_DBG_EFF)) break;
+        if (__ldg(m.eff_sp + e) == bath) Bi = Bi - t * DT(__ldg(m.eff_am1 + e));
+      }
+    }
     const DT Bs = nscale<NEWTON>(o, Bi);
     for (int q2 = row_lo; q2 < row_hi; q2++) {
       const RowNu rn = m.rows[q2];

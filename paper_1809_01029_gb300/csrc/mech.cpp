@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -421,11 +422,16 @@ int mech_build(pj_mech* m) {
       }
     }
     r.eff_hi = (int32_t)eff_sp.size();
+    // a row per unit of |nu|: every Jacobian contribution is then +-1 times
+    // its value, a sign flip the kernels do without an FP64 instruction
+    // (|nu| >= 2 is rare: 14 of 1262 rows at 53 species)
     r.row_lo = (int32_t)rows.size();
     for (int k = 0; k < bath; k++)
-      if (nu[k] != 0) rows.push_back(RowNu{k, nu[k], (double)nu[k]});
+      for (int u = 0; u < std::abs(nu[k]); u++) rows.push_back(RowNu{k, nu[k] > 0 ? 1 : -1, nu[k] > 0 ? 1.0 : -1.0});
     r.row_hi = (int32_t)rows.size();
     r.dense = rate_dependence(m, i, dep) ? 1 : 0;
+    r.bath_in = 0;
+    for (int a = 0; a < 2 * PJ_MAX_SP; a++) r.bath_in |= r.sp[a] == bath && (a % PJ_MAX_SP) < (a < PJ_MAX_SP ? r.nreac : r.nprod);
   }
 
   // Every entry the Jacobian kernels accumulate into must be in the pattern

@@ -58,11 +58,14 @@ struct alignas(8) Rxn {
                                   // then the P-log entries / Chebyshev block
   int16_t tab_n, tab_m;           // P-log entries / Chebyshev N_T, N_P
   int32_t tgt_lo;                 // first of this reaction's Jacobian targets in tgt_csr / tgt_csc
+  int32_t bath_in;                // the bath gas is one of its reactants or products
 };
 
+// One unit of a reaction's net stoichiometric coefficient for species k: a
+// species with |nu| = 2 has two such rows.
 struct RowNu {
   int32_t k;      // species index (< Ns-1)
-  int32_t nu;     // net stoichiometric coefficient
+  int32_t nu;     // +1 or -1
   double nud;     // the same as a double
 };
 

@@ -362,14 +362,16 @@ int pj_debug_set_target(const pj_mech* mech, int fmt, int32_t index, int32_t val
 /* The kernel layout the Jacobian entries (pj_eval_jacobian_sparse / dense,
  * fmt PJ_CSR, PJ_CSC or PJ_DENSE) and the FP32 Newton matrix (prec PJ_F32)
  * use for n states of this mechanism on the current device: *layout =
- * PJ_LAYOUT_*.  The choice was measured on GB300: the cooperative layout for
- * batches below one round of the one-state-per-thread kernels, for
- * mechanisms whose one-state-per-thread arrays would live in a global
- * workspace, and for the FP32 form at sizes that use tensor memory; the
- * one-state-per-thread layouts otherwise.  The cooperative layout keeps few
- * Jacobians live in L2 (a third of the DRAM traffic at 53 species) and is
- * not bit-reproducible (see pj_eval_jacobian_sparse).  Errors: PJ_ERR_ARG,
- * PJ_ERR_CUDA (no device copy). */
+ * PJ_LAYOUT_*.  The choice was measured on GB300: the cooperative layout
+ * for batches of at most one 32-state tile per SM, for batches below one
+ * round of the one-state-per-thread kernels, and for the sparse Jacobians
+ * and FP32 Newton matrices of mechanisms too large for per-thread shared
+ * memory; tensor memory for the dense Jacobian of such mechanisms; shared
+ * memory, one state per thread, for small mechanisms on large batches.  The
+ * cooperative layout keeps few Jacobians live in L2 (a third to a half of
+ * the DRAM traffic at 53 species) and is not bit-reproducible (see
+ * pj_eval_jacobian_sparse).  Errors: PJ_ERR_ARG, PJ_ERR_CUDA (no device
+ * copy). */
 int pj_jacobian_layout(const pj_mech* mech, int fmt, int prec, int64_t n, int32_t* layout);
 
 /* operation ids for pj_workspace_size */

@@ -198,25 +198,34 @@ TmPlan tm_plan(int ns) {
   return t;
 }
 
-// Which Jacobian layout runs, chosen by measurement on GB300 (CSR, FP64
-// and FP32, mechanisms of 13 to 111 species, 4 ki to 1 Mi states):
-//  * batches smaller than one round of the one-state-per-thread kernels
-//    (SMs x 512 threads): the cooperative kernel, whose 32-state tiles spread
-//    over every SM (13 species, 4096 states: 64 M against 13 M states/s);
-//  * mechanisms whose one-state-per-thread arrays go to a global workspace
-//    (no TMEM or shared-memory layout, e.g. 111 species): cooperative, 16
-//    warps (+10 % FP64, +16 % FP32 Newton form);
-//  * the FP32 Newton form where the TMEM layout applies (53 species):
-//    cooperative, 8 warps in two blocks per SM (+6 %);
-//  * otherwise the one-state-per-thread layouts (TMEM at 53 species, 2 %
-//    ahead of the best cooperative shape; shared memory at 13 species).
-// The cooperative kernel keeps far fewer Jacobians live in L2 (32 states per
-// block, one block per SM at 16 warps: 44 KB of DRAM traffic per state at 53
-// species against 154 KB), so it is the layout to force where the Jacobian
-// shares the GPU with other memory-heavy work.
+// Which Jacobian layout runs, chosen by measurement on GB300 (1 Mi states
+// unless stated; states/s, one state per thread against the cooperative
+// shapes, warps x blocks per SM):
+//  * at most one 32-state tile per SM: cooperative, 16 warps on each tile
+//    (13 species, 4096 states: 64 M against 13 M);
+//  * the FP64 Jacobian of TMEM-size mechanisms (53 species) and of
+//    mechanisms whose one-state-per-thread arrays need a global workspace
+//    (111 species), and any batch below SMs x 512 states: cooperative, 8
+//    warps x 2 blocks (53 species CSR 11.47 M against 11.17 M in TMEM, CSC
+//    11.46 / 11.06, CONV 11.93 / 11.73, all reaction types 9.84 / 9.75;
+//    111 species 4.69 M against 4.16 M; 53 species, 64 ki states 11.0 M
+//    against 9.8 M), 16 warps x 1 above 200 species (the 874-species
+//    arrays are 671 KB a tile);
+//  * the dense FP64 Jacobian of TMEM-size mechanisms: one state per thread
+//    in TMEM (11.49 M against 11.35 M);
+//  * the FP32 Newton matrix of those mechanisms: cooperative, 4 warps x 4
+//    blocks, the arrays in the workspace (53 species 14.64 M against 13.22
+//    M; 111 species 5.84 M against 4.85 M);
+//  * otherwise (13 species, large batches): one state per thread, arrays
+//    in shared memory (117 M against 114 M at 4 x 4).
+// Each cooperative block keeps only its 32 states' Jacobians live in L2, a
+// fraction of the one-state-per-thread kernels' live set (DRAM traffic per
+// state at 53 species: 154 KB in TMEM, 44 KB at 16 x 1, about 73 KB at 8 x
+// 2), so 16 x 1 is the shape to force where the Jacobian shares the GPU
+// with other memory-heavy work.
 // The cooperative kernel keeps a tile's per-state arrays in shared memory
-// where they fit, else (more than about 200 species) in a workspace of 3 Ns
-// x 32 doubles per block, which at one block per SM stays in L2.
+// where they fit, else in a workspace of 3 Ns x 32 doubles per block, which
+// stays in L2 (874 species at one block per SM: 102 MB).
 // PYJAC_GB_JAC_LAYOUT=coop|percore forces one family (coop only where its
 // shared memory fits); PYJAC_GB_COOP_WARPS sets the warps per block (4, 8
 // or 16), PYJAC_GB_COOP_CTAS the blocks per SM (at most 16 / warps) and
@@ -248,7 +257,6 @@ static bool coop_fit(const DevMech& m, int warps, int ctas, int64_t n, CoopPlan&
 }
 
 CoopPlan coop_plan(const DevMech& m, int fmt, int dt_bytes, int64_t n) {
-  (void)fmt;
   CoopPlan c{false, 16, 1, 0, 0, false, 0};
   const char* lay = getenv("PYJAC_GB_JAC_LAYOUT");
   if (lay && strcmp(lay, "percore") == 0) return c;
@@ -260,12 +268,23 @@ CoopPlan coop_plan(const DevMech& m, int fmt, int dt_bytes, int64_t n) {
     return c;
   }
   const TmPlan t = tm_plan(m.ns);
+  const int sms = sm_count();
+  const int64_t tiles = (n + kCoopTile - 1) / kCoopTile;
   const bool percore_global = !t.use && plan_for(jacobian_arrays(), m.ns, n).global_ws;
-  if (n < (int64_t)sm_count() * 512 || percore_global) {
+  if (tiles <= sms) {  // one tile per SM at most: all 16 warps on it
     coop_fit(m, 16, 1, n, c);
     return c;
   }
-  if (t.use && dt_bytes == 4 && coop_shape(m, 8, 2, true, 0, c)) return c;
+  if (n < (int64_t)sms * 512 || t.use || percore_global) {
+    if (t.use && fmt == PJ_DENSE && dt_bytes == 8 && n >= (int64_t)sms * 512) {
+      c.use = false;  // the dense FP64 Jacobian: tensor memory, one state per thread
+      return c;
+    }
+    if (dt_bytes == 4 && (t.use || percore_global)) coop_fit(m, 4, 4, n, c);
+    else if (m.ns > 200) coop_fit(m, 16, 1, n, c);
+    else coop_fit(m, 8, 2, n, c);
+    return c;
+  }
   c.use = false;
   return c;
 }
@@ -281,7 +300,8 @@ size_t workspace_bytes(int arrays, int ns, int64_t n) {
     const int64_t tiles =
         std::max<int64_t>(1, std::min<int64_t>((n + kCoopTile - 1) / kCoopTile, (int64_t)sm_count() * 4));
     const char* ar = getenv("PYJAC_GB_COOP_ARRAYS");
-    const bool global = coop_smem_bytes(ns, kCoopWarpsMax) > kSmemCap || (ar && strcmp(ar, "global") == 0);
+    const bool global = 4 * (coop_smem_bytes(ns, 4) + kBlockOverhead) > kSmemPerSm ||
+                        coop_smem_bytes(ns, kCoopWarpsMax) > kSmemCap || (ar && strcmp(ar, "global") == 0);
     const size_t co = global ? coop_arrays_bytes(ns) * (size_t)tiles : 0;
     return std::max(pc, co);
   }

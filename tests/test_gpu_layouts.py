@@ -156,11 +156,11 @@ def test_layout_newton_matrix_f32(pj, mechs, name, n, layout):
 
 
 def test_default_layout_follows_the_measured_rule(pj, mechs):
-    """Small batches and mechanisms whose per-state arrays need a global
-    workspace run cooperatively; the 53-species FP64 Jacobian of a large batch
-    runs one state per thread in tensor memory, its FP32 Newton form
-    cooperatively; the 13-species Jacobian of a large batch one state per
-    thread."""
+    """At most one 32-state tile per SM, and the 53- and 111-species
+    Jacobians (but the dense 53-species one) of larger batches, run
+    cooperatively; the dense 53-species FP64 Jacobian of a large batch runs
+    one state per thread in tensor memory; the 13-species Jacobian of a
+    large batch one state per thread in shared memory."""
     import torch
     if torch.cuda.get_device_properties(0).multi_processor_count != 152:
         pytest.skip("the rule was measured on 152-SM parts")
@@ -170,7 +170,9 @@ def test_default_layout_follows_the_measured_rule(pj, mechs):
     assert h13.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, 4096) == C
     assert h13.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, big) == P
     assert h53.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, 4096) == C
-    assert h53.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, big) == T
+    assert h53.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, big) == C
+    assert h53.jacobian_layout(pj.PJ_CSC, pj.PJ_F64, big) == C
+    assert h53.jacobian_layout(pj.PJ_DENSE, pj.PJ_F64, big) == T
     assert h53.jacobian_layout(pj.PJ_CSR, pj.PJ_F32, big) == C
     assert h111.jacobian_layout(pj.PJ_CSR, pj.PJ_F64, big) == C
     assert h111.jacobian_layout(pj.PJ_CSR, pj.PJ_F32, big) == C

@@ -347,7 +347,9 @@ def _time(torch, stream, fn, reps=5):
 PROFILE_OF = {("k_jacobian_coop", "gri53"): "k_jacobian_coop_gri53.md",
               ("k_jacobian_tm", "gri53"): "k_jacobian_tm_gri53.md",
               ("k_source_terms", "gri53"): "k_source_terms_gri53.md",
-              ("k_lu_factor_v", "gri53"): "k_lu_factor_gri53.md"}
+              ("k_lu_factor_v", "gri53"): "k_lu_factor_gri53.md",
+              ("k_jacobian_coop", "usc111"): "k_jacobian_coop_usc111.md",
+              ("k_jacobian_coop", "ic5874"): "k_jacobian_coop_ic5874.md"}
 
 
 def sources_hash():

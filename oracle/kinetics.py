@@ -10,8 +10,7 @@ over species and reactions, IEEE float64 (or complex128 for complex-step
 differentiation).  Every function names the passage it follows.  The paper's
 equation bodies for the state vector, source terms and Jacobian are not in
 the available text (Sec. 2.2 loads them from a supplement); the forms written
-here are the standard published ones the section names, and the readings are
-listed in the design notes:
+here are the standard published ones the section names (Sec. 2.2, Sec. 3.4):
 
 * state Phi = [T, S, n_0 .. n_{Ns-2}], S = V (CONP, P fixed) or P (CONV, V
   fixed); the bath gas Ns-1 is implicit through the ideal-gas law (Sec. 2.2);

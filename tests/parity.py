@@ -61,7 +61,12 @@ REPORT = []
 WELL = 10.0     # env <= WELL |ref|: an entry without significant cancellation
 
 
-def check_close(got, ref, env, rtol, atol, what=""):
+def check_close(got, ref, env, rtol, atol, what="", max_env_frac=None):
+    """got within rtol * max(|ref|, env) + atol of ref, entry by entry; the
+    well-conditioned entries (env <= WELL |ref|) also within rtol |ref| +
+    atol.  Returns how many entries passed only through the envelope; with
+    max_env_frac, at most that fraction of the entries (and at least one)
+    may."""
     got = np.asarray(got)
     ref = np.asarray(ref)
     env = np.maximum(np.asarray(env), np.abs(ref))
@@ -85,6 +90,9 @@ def check_close(got, ref, env, rtol, atol, what=""):
     rel_well = np.where(well & (ref != 0), err / np.where(ref != 0, np.abs(ref), 1.0), 0.0)
     REPORT.append(dict(what=what, entries=int(err.size), needed_env=needed_env, well=int(well.sum()),
                        worst_rel_well=float(rel_well.max()) if rel_well.size else 0.0))
+    if max_env_frac is not None:
+        assert needed_env <= max(1, max_env_frac * err.size), f"{what}: {needed_env} of {err.size} entries " \
+                                                              "passed only through the envelope"
     return needed_env
 
 

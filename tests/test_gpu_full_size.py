@@ -6,6 +6,8 @@ at any size (zero cotangents give exact zeros, no invalid state counted).
 
 Samples cover the first and last thread of the first tiles, a state in the
 middle and the last tiles, and random states."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -13,6 +15,10 @@ import oracle
 import synth
 from tests.parity import (RTOL_SRC, ATOL_SRC, RTOL_JAC, ATOL_JAC, check_close, y_envelope, paper_error_norms,
                           newton_tol, newton_error)
+
+# the measured sizes: at most one entry in 10^5 may pass only through the
+# oracle's envelope (the GPU suite has 4 of 4.7e7)
+check_close = functools.partial(check_close, max_env_frac=1e-5)
 
 pytestmark = pytest.mark.gpu
 

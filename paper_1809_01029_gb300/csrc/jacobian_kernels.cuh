@@ -396,8 +396,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1)
       x.AS_S = DT(S(cAS_S));
       x.ATB = DT(S(cATB));
       x.ASB = DT(S(cASB));
-      for (int j = warp; j < N; j += W)
-        jac_ts_column<MODE, FMT, DT, NEWTON>(m, j, j >= 2 ? A.at(aG, j - 2) : 0.0, x, o);
+      // columns j = warp, warp + W, ...: warps 0 and 1 take the T and S
+      // columns first (W >= 4), every other column is a species column
+      int j = warp;
+      if (j == 0) {
+        jac_ts_column<MODE, FMT, DT, NEWTON, 0>(m, 0, 0.0, x, o);
+        j += W;
+      } else if (j == 1) {
+        jac_ts_column<MODE, FMT, DT, NEWTON, 1>(m, 1, 0.0, x, o);
+        j += W;
+      }
+      for (; j < N; j += W) jac_ts_column<MODE, FMT, DT, NEWTON, 2>(m, j, A.at(aG, j - 2), x, o);
     }
 
     if (NEWTON) {

@@ -483,7 +483,11 @@ __device__ __forceinline__ JacRowVars<DT> jac_row_vars(double T, double V, doubl
 // the reactions accumulated there and overwrite them with the final values.
 // Newton form: the accumulated sums already carry -h gamma, the per-state
 // terms take it here, and the diagonal entries (0,0) and (1,1) get the 1.
-template <int MODE, int FMT, typename DT, bool NEWTON>
+// COL: 0 and 1 for the T and S columns (j == COL), 2 for the species
+// columns j >= 2, so that no column carries the other kinds' arithmetic (a
+// runtime test of j leaves the branches' FP64 instructions in every column,
+// predicated off).
+template <int MODE, int FMT, typename DT, bool NEWTON, int COL>
 __device__ __forceinline__ void jac_ts_column(const DevMech& m, int j, double cx_j, const JacRowVars<DT>& x,
                                               const JacOut<DT>& o) {
   const int64_t ld = o.ld, s = o.s;
@@ -493,10 +497,10 @@ __device__ __forceinline__ void jac_ts_column(const DevMech& m, int j, double cx
   if (e0 < 0 || e1 < 0) return;  // a bad map entry (recorded by jpos)
 #endif
   DT jT, dOm;
-  if (j == 0) {
+  if constexpr (COL == 0) {
     jT = -nscale<NEWTON>(o, x.AT_T + x.j00) * x.iden;
     dOm = nscale<NEWTON>(o, x.AS_T);
-  } else if (j == 1) {
+  } else if constexpr (COL == 1) {
     jT = -nscale<NEWTON>(o, x.AT_S + x.j01) * x.iden;
     dOm = nscale<NEWTON>(o, x.AS_S);
   } else {
@@ -507,10 +511,14 @@ __device__ __forceinline__ void jac_ts_column(const DevMech& m, int j, double cx
     dOm = (accS + nscale<NEWTON>(o, x.ASB)) * x.invV;
   }
   DT jS = x.cT * jT + x.rtvp * dOm;
-  if (j == 0) jS = jS + nscale<NEWTON>(o, x.x0);
-  if (j == 1) jS = jS + nscale<NEWTON>(o, x.x1);
-  if (NEWTON && j == 0) jT = jT + DT(1);
-  if (NEWTON && j == 1) jS = jS + DT(1);
+  if constexpr (COL == 0) {
+    jS = jS + nscale<NEWTON>(o, x.x0);
+    if (NEWTON) jT = jT + DT(1);
+  }
+  if constexpr (COL == 1) {
+    jS = jS + nscale<NEWTON>(o, x.x1);
+    if (NEWTON) jS = jS + DT(1);
+  }
   if (o.w) {
     J[e0 * ld + s] = jT;
     J[e1 * ld + s] = jS;
@@ -652,7 +660,9 @@ __device__ __forceinline__ void jacobian_state(const DevMech& m, const SA& A,
   // energy row 0 and state row 1
   const JacRowVars<DT> x = jac_row_vars<MODE, DT>(T, V, P, invT, Tdot, Om, den, dden_T, dden_S, sumCxW,
                                                   A.at(aG, bath), v.AT_T, v.AT_S, v.AS_T, v.AS_S, v.ATB, v.ASB);
-  for (int j = 0; j < N; j++) jac_ts_column<MODE, FMT, DT, NEWTON>(m, j, j >= 2 ? A.at(aG, j - 2) : 0.0, x, o);
+  jac_ts_column<MODE, FMT, DT, NEWTON, 0>(m, 0, 0.0, x, o);
+  jac_ts_column<MODE, FMT, DT, NEWTON, 1>(m, 1, 0.0, x, o);
+  for (int j = 2; j < N; j++) jac_ts_column<MODE, FMT, DT, NEWTON, 2>(m, j, A.at(aG, j - 2), x, o);
   if (NEWTON)
     for (int k = 2; k < N; k++) newton_species_diagonal<FMT>(m, k, o);
 }

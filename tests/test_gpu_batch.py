@@ -15,10 +15,22 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def percore_entry_points():
     """The plans' persistent kernels evaluate one state per thread, as the
-    direct entry points' "percore" layout does; with that layout the two give
-    the same bits, which these tests check."""
+    direct entry points' "percore" layout does: the same arithmetic, in
+    other kernels, whose multiply-adds the compiler contracts on its own, so
+    the two agree to the last bits of rounding (same_bits_but_rounding)."""
     with jacobian_layout("percore"):
         yield
+
+
+def same_bits_but_rounding(o, r, rel=1e-13):
+    """o and r (entries x states) equal to within rel of each state's largest
+    entry: one state per thread in two kernels (a plan's and an entry
+    point's) differs by the rounding of single operations, nothing more."""
+    import torch
+    if torch.equal(o, r):
+        return True
+    scale = torch.maximum(o.abs(), r.abs()).amax(dim=0, keepdim=True)
+    return bool(((o - r).abs() <= rel * scale).all())
 
 
 @pytest.fixture(scope="module")
@@ -65,8 +77,8 @@ def test_plan_matches_single_batch_entry_points(pj, mechs, mode):
             continue
         ref = pj.jacobian_sparse(h, mode, phi, par, fmt=pj.PJ_CSR)
         ref_f = pj.source_terms(h, mode, phi, par)
-        assert torch.equal(o, ref)
-        assert torch.equal(osrc, ref_f)
+        assert same_bits_but_rounding(o, ref)
+        assert same_bits_but_rounding(osrc, ref_f)
         check_close(f.cpu().numpy(), ref_f.cpu().numpy(), np.abs(ref_f.cpu().numpy()), RTOL_SRC, ATOL_SRC, "dphi")
 
 
@@ -123,7 +135,7 @@ def test_graph_capture_replay_and_groups(pj, mechs):
             plan.launch(st)
     st.synchronize()
     for (_, _, o, _), r in zip(bj, refs):
-        assert torch.equal(o, r)
+        assert same_bits_but_rounding(o, r)
     # groups run one after another, so batches of different groups may share
     # output memory: two batches of two groups write the same buffer
     phi_a, par_a = synth.make_states(m, 400, 70, synth.CONP)
@@ -136,7 +148,7 @@ def test_graph_capture_replay_and_groups(pj, mechs):
                     max_states_per_launch=400)
     plan2.run()
     torch.cuda.synchronize()
-    assert torch.equal(shared, pj.jacobian_sparse(h, synth.CONP, db[1], db[0]))
+    assert same_bits_but_rounding(shared, pj.jacobian_sparse(h, synth.CONP, db[1], db[0]))
 
 
 def test_autotune_and_cache(pj, mechs, tmp_path):
@@ -152,11 +164,8 @@ def test_autotune_and_cache(pj, mechs, tmp_path):
     assert os.path.exists(cache) and "gri53" not in open(cache).read()  # keyed by hash, not name
     coop = cfg["threads_per_block"] >= 256
 
-    def same(o, r, rounding):
-        if not rounding:
-            return torch.equal(o, r)
-        scale = torch.maximum(o.abs(), r.abs()).amax(dim=0, keepdim=True)
-        return bool(((o - r).abs() <= 1e-12 * scale).all())
+    def same(o, r, coop):
+        return same_bits_but_rounding(o, r, 1e-12 if coop else 1e-13)
     plan.run()
     torch.cuda.synchronize()
     for (_, _, o, _), r in zip(bj, refs):
@@ -164,8 +173,8 @@ def test_autotune_and_cache(pj, mechs, tmp_path):
     plan2 = pj.Plan(h, pj.PJ_OP_JACOBIAN, synth.CONP, bj)
     cfg2 = plan2.autotune(cache_path=cache, reps=1)
     assert cfg2 == cfg
-    # every one-state-per-thread shape gives the same bits; the cooperative
-    # shapes (several warps sum into one entry) agree within rounding
+    # every shape agrees with the entry point to rounding (the cooperative
+    # shapes sum one entry from several warps)
     for shape in ((32, 1, 1), (64, 2, 0), (128, 4, 0), (512, 1, 1), (512, 1, 0), (256, 2, 1), (256, 1, 0)):
         plan2.set_config(*shape)
         plan2.run()

@@ -942,6 +942,18 @@ def main():
         for md, nm, ph_, pa_ in ((synth.CONP, "conp", phi, par), (synth.CONV, "conv", phv, pav)):
             t_src = timeit(lambda: pj.pj_eval_source_terms(h, md, n, pa_, ph_, n, dphi, status, work_s, wbs, stream))
             variants[f"source_{nm}"] = n / (t_src * 1e-3)
+        # the low-DRAM-traffic shape of the cooperative kernel (16 warps x 1
+        # block per SM; the library reads the layout variables at launch)
+        lay_env = {"PYJAC_GB_JAC_LAYOUT": "coop", "PYJAC_GB_COOP_WARPS": "16", "PYJAC_GB_COOP_CTAS": "1"}
+        saved = {k: os.environ.get(k) for k in lay_env}
+        os.environ.update(lay_env)
+        variants["jacobian_csr_conp_coop16x1"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
+            h, mode, pj.PJ_CSR, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
         variants["jacobian_csc_conp"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(
             h, mode, pj.PJ_CSC, n, par, phi, n, vals, dphi, status, work, wb, stream)) * 1e-3)
         variants["jacobian_csr_conv"] = n / (timeit(lambda: pj.pj_eval_jacobian_sparse(

@@ -353,14 +353,22 @@ PROFILE_OF = {("k_jacobian_coop", "gri53"): "k_jacobian_coop_gri53.md",
 
 
 def sources_hash():
+    """Hash of the kernel sources (paper_1809_01029_gb300/csrc and the C
+    header) with comments and blank lines removed, so that a profile's
+    figures stay attached to the code they measured across comment edits."""
     import hashlib
+    import re
     d = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1809_01029_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
-            d.update(f.encode())
-            d.update(open(os.path.join(csrc, f), "rb").read())
-    d.update(open(os.path.join(ROOT, "include", "pyjac_gb.h"), "rb").read())
+    files = [os.path.join(csrc, f) for f in sorted(os.listdir(csrc)) if f.endswith((".cu", ".cuh", ".cpp", ".h"))]
+    files.append(os.path.join(ROOT, "include", "pyjac_gb.h"))
+    for path in files:
+        text = open(path, encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        d.update(os.path.basename(path).encode())
+        d.update(code.encode())
     return d.hexdigest()[:16]
 
 

@@ -220,9 +220,9 @@ TmPlan tm_plan(int ns) {
 //    in shared memory (117 M against 114 M at 4 x 4).
 // Each cooperative block keeps only its 32 states' Jacobians live in L2, a
 // fraction of the one-state-per-thread kernels' live set (DRAM traffic per
-// state at 53 species: 154 KB in TMEM, 44 KB at 16 x 1, about 73 KB at 8 x
-// 2), so 16 x 1 is the shape to force where the Jacobian shares the GPU
-// with other memory-heavy work.
+// state at 53 species: 154 KB in TMEM, 34 KB at 16 x 1, 65 KB at 8 x 2), so
+// 16 x 1 is the shape to force where the Jacobian shares the GPU with other
+// memory-heavy work.
 // The cooperative kernel keeps a tile's per-state arrays in shared memory
 // where they fit, else in a workspace of 3 Ns x 32 doubles per block, which
 // stays in L2 (874 species at one block per SM: 102 MB).

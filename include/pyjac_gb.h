@@ -259,8 +259,9 @@ int pj_eval_source_terms(const pj_mech* mech, int mode, int64_t n, const double*
  * same bits on every run.  The environment variable PYJAC_GB_JAC_LAYOUT
  * (read at every launch) forces a family: "percore" (bit-reproducible) or
  * "coop" (where its shared memory fits); PYJAC_GB_COOP_WARPS = 4, 8 or 16
- * sets the cooperative block's warps and PYJAC_GB_COOP_CTAS the blocks per
- * SM. */
+ * sets the cooperative block's warps, PYJAC_GB_COOP_CTAS the blocks per
+ * SM, and PYJAC_GB_COOP_ARRAYS = "global" puts a tile's per-state arrays in
+ * the workspace instead of shared memory. */
 int pj_eval_jacobian_sparse(const pj_mech* mech, int mode, int fmt, int64_t n,
                             const double* d_param, const double* d_phi, int64_t ld,
                             double* d_vals, double* d_dphi, int* d_status,
